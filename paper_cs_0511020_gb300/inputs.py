@@ -1,0 +1,106 @@
+"""Seeded synthetic inputs for the Pbit list sort (shared by tests, bench and
+smoke; holds none of the sort's arithmetic).
+
+A list lives in a node pool: ``next[v]`` is the pool index of v's successor
+(-1 = NULL) and ``key[v]`` its key (paper, Sec. "Structure of data
+representing a node").  All generators are numpy PCG64 streams seeded with
+``0x0511020 + workload id`` unless a seed is given.
+
+Workloads (sizes as the paper's experiments scale them up to the GPU):
+  1  2^20 nodes, AoS {int32 next; uint32 key}, random list order, uniform u32
+  2  2^27 nodes, SoA, random order (and the push-built order), uniform u32
+  3  2^26 nodes u64 Zipf(1.1) over 1024 values with a constant top half;
+     2^26 nodes u8 uniform
+  4  4096 lists in one pool, lengths log-uniform in [16, 2^20], uniform u32
+  5  request stream: Poisson arrivals, lengths log-uniform in [2^4, 2^24],
+     key types u16:u32:u64 = 1:2:1
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 0x0511020
+_UINT = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def list_from_order(order: np.ndarray, pool_size: int | None = None):
+    """next[] with next[order[i]] = order[i+1] and the last node -> -1."""
+    order = np.asarray(order, dtype=np.int32)
+    size = order.size if pool_size is None else pool_size
+    nxt = np.full(size, -1, dtype=np.int32)
+    if order.size:
+        nxt[order[:-1]] = order[1:]
+    return nxt, (int(order[0]) if order.size else -1)
+
+
+def random_list(n: int, seed: int):
+    """A list over pool indices 0..n-1 in a seeded random order."""
+    return list_from_order(rng(seed).permutation(n).astype(np.int32))
+
+
+def push_built_list(n: int):
+    """The list that pushing pool nodes 0..n-1 onto an empty list builds
+    (paper, Sec. 2 push): root = n-1, next[v] = v-1, next[0] = -1."""
+    nxt = np.arange(-1, n - 1, dtype=np.int32)
+    return nxt, (n - 1 if n else -1)
+
+
+def uniform_keys(n: int, key_bytes: int, seed: int) -> np.ndarray:
+    dt = _UINT[key_bytes]
+    return rng(seed).integers(0, np.iinfo(dt).max, size=n, dtype=dt, endpoint=True)
+
+
+def zipf_u64_keys(n: int, seed: int, distinct: int = 1024, s: float = 1.1,
+                  top: int = 0xA5A5A5A5) -> np.ndarray:
+    """u64 keys: constant top 32 bits, low 32 bits one of ``distinct`` seeded
+    values; value ranks drawn Zipf(s) by inverse CDF, rank -> value random."""
+    g = rng(seed)
+    vals = np.unique(g.integers(0, 1 << 32, size=4 * distinct, dtype=np.uint64))
+    vals = g.permutation(vals)[:distinct]
+    w = 1.0 / np.arange(1, distinct + 1, dtype=np.float64) ** s
+    cdf = np.cumsum(w / w.sum())
+    ranks = np.searchsorted(cdf, g.random(n), side="right").clip(0, distinct - 1)
+    return (np.uint64(top) << np.uint64(32)) | vals[ranks]
+
+
+def aos_pack(nxt: np.ndarray, key_u32: np.ndarray) -> np.ndarray:
+    """Interleave into the 8-byte AoS node {int32 next; uint32 key}."""
+    a = np.empty((nxt.size, 2), dtype=np.int32)
+    a[:, 0] = nxt
+    a[:, 1] = key_u32.view(np.int32)
+    return a
+
+
+def log_uniform_lengths(count: int, lo_log2: float, hi_log2: float, seed: int,
+                        lo: int, hi: int) -> np.ndarray:
+    u = rng(seed).random(count)
+    return np.clip(np.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * u)), lo, hi).astype(np.int64)
+
+
+def batched_pool(lengths: np.ndarray, key_bytes: int, seed: int):
+    """Lists packed into one pool: list i owns [off[i], off[i+1]) with a
+    random order inside it.  Returns (next, key, roots, offsets)."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    off = np.zeros(lengths.size + 1, dtype=np.int64)
+    np.cumsum(lengths, out=off[1:])
+    total = int(off[-1])
+    g = rng(seed)
+    # one random permutation per list, built from a global random key sort
+    # inside each range (vectorised: sort (list id, random) pairs)
+    r = g.random(total)
+    lid = np.repeat(np.arange(lengths.size, dtype=np.int64), lengths)
+    perm = np.lexsort((r, lid)).astype(np.int64)      # positions grouped by list, random inside
+    nxt = np.full(total, -1, dtype=np.int32)
+    # within list i, perm[off[i]:off[i+1]] is a random order of its pool range
+    has_succ = np.ones(total, dtype=bool)
+    has_succ[off[1:][lengths > 0] - 1] = False
+    src = perm[has_succ]
+    dst = np.roll(perm, -1)[has_succ]
+    nxt[src] = dst.astype(np.int32)
+    roots = np.where(lengths > 0, perm[np.minimum(off[:-1], max(total - 1, 0))], -1).astype(np.int32)
+    key = uniform_keys(total, key_bytes, seed + 1)
+    return nxt, key, roots, off
