@@ -1,0 +1,159 @@
+/*
+ * pbit.h -- C ABI of the GB300 Pbit list sort.
+ *
+ * Pbit ("Pbit and other list sorting algorithms", D. S. Planeta) sorts a
+ * singly-linked list of {next, data} nodes by splitting it on K-bit digits of
+ * the key, most significant digit first, recursing into every bucket and
+ * finally concatenating the sorted fragments (Sec. "The idea of sorting using
+ * Pbit", Sec. "Implementation in C++", Sec. 5.1 "Function merge").  This
+ * library computes the same result -- the list relinked in ascending order of
+ * the low M bits of the key, equal keys kept in list order -- with GPU
+ * kernels: list ranking, MSD digit passes, shared-memory finishing of small
+ * buckets and a relink (next[s[i]] = s[i+1]).
+ *
+ * Conventions shared by every call
+ *   - A node pool is caller-owned DEVICE memory: int32 successor indices
+ *     (-1 = NULL) and keys of 1, 2, 4 or 8 bytes (unsigned unless
+ *     PBIT_SIGNED).  SoA: next_stride_bytes = 4, key_stride_bytes = key
+ *     width.  AoS {int32 next; uint32 key}: both strides 8, key = next + 4.
+ *     Strides must be multiples of the element width.
+ *   - next[] is relinked IN PLACE; key[] is only read.
+ *   - 1 <= K <= 16, K divides M, 1 <= M <= 8 * key width; otherwise
+ *     PBIT_EINVAL.  The result does not depend on K (K only fixes the paper's
+ *     digit width); the GPU's own digit width is a tuning choice.
+ *   - Before anything is written to next[], the list shape is validated (every
+ *     index in range, no cycle, exactly n nodes reachable from the root).  On
+ *     any error next[] is left untouched and no root is written.
+ *   - Calls are stream-ordered on the given stream (a cudaStream_t passed as
+ *     void*, NULL = legacy default stream); calls that return a status read it
+ *     back and therefore synchronize that stream.
+ *   - The library never throws, and the sort calls never allocate device
+ *     memory: the caller passes a workspace of pbit_workspace_size() bytes
+ *     (256-byte aligned device memory).  Workspaces must not be shared by
+ *     calls that may run concurrently.
+ */
+#ifndef PBIT_H
+#define PBIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PBIT_OK = 0,
+    PBIT_EINVAL = 1,   /* bad argument (M, K, sizes, strides, pointers)           */
+    PBIT_ENOMEM = 2,   /* workspace too small / server arena exhausted            */
+    PBIT_EBADLIST = 3, /* cycle, wrong length, index out of range, bad root       */
+    PBIT_ETIMEOUT = 4, /* a bounded device wait gave up                            */
+    PBIT_ECUDA = 5,    /* a CUDA runtime call failed                               */
+    PBIT_EAGAIN = 6,   /* server: request not admitted (queue full / over budget)  */
+    PBIT_EPENDING = 7  /* server: request still running                            */
+} pbit_status;
+
+typedef enum { PBIT_U8 = 1, PBIT_U16 = 2, PBIT_U32 = 4, PBIT_U64 = 8 } pbit_key_type;
+
+/* pool flags */
+#define PBIT_SIGNED 1     /* keys are two's complement (needs M = 8 * width)     */
+#define PBIT_DESCENDING 2 /* largest key first; equal keys still in list order   */
+#define PBIT_DOUBLY 4     /* pool has prev[]: it is rebuilt after the relink     */
+#define PBIT_FLOAT 8      /* keys are IEEE-754 binary32/binary64 (width 4 or 8)   */
+
+typedef struct {
+    int32_t *next;            /* device: successor index, -1 = NULL              */
+    int64_t next_stride_bytes;/* 4 (SoA) or 8 (AoS)                                */
+    const void *key;          /* device: keys                                      */
+    int64_t key_stride_bytes; /* key width (SoA) or 8 (AoS)                        */
+    int32_t key_type;         /* pbit_key_type                                     */
+    int32_t flags;            /* PBIT_SIGNED | PBIT_DESCENDING | PBIT_DOUBLY ...   */
+    int64_t pool_size;        /* number of nodes in the pool, < 2^31               */
+    int32_t *prev;            /* device, only with PBIT_DOUBLY: predecessor index  */
+    int64_t prev_stride_bytes;/* only with PBIT_DOUBLY                              */
+} pbit_pool;
+
+/* Tuning knobs; any field <= 0 takes the built-in / autotuned default. */
+typedef struct {
+    int32_t digit_bits;   /* GPU digit width per MSD pass: 4 (16 buckets) or 8   */
+    int32_t smem_cutoff;  /* buckets <= this many nodes are finished in smem     */
+    int32_t ruler_stride; /* list ranking: one ruler per this many nodes (2^k)   */
+    int32_t reserved;
+} pbit_tune;
+
+/* Human-readable name of a status code (static string). */
+const char *pbit_status_string(int status);
+
+/*
+ * Workspace bytes needed to sort up to `pool_size` nodes in `num_lists` lists
+ * with keys of `key_type`, for the given tune (NULL = defaults).
+ * Returns PBIT_OK or PBIT_EINVAL.
+ */
+pbit_status pbit_workspace_size(int64_t pool_size, int32_t num_lists, int32_t key_type,
+                                const pbit_tune *tune, size_t *bytes);
+
+/*
+ * Sort ONE list (Sec. "Complete Pbit implementation": Pbit(L) returning the
+ * new head).  The list starts at `root` and must contain exactly `n` nodes,
+ * and n must equal pool->pool_size (every pool node is on the list).
+ * root = -1 with n = 0 returns -1 (an empty list, as in the paper).
+ * On PBIT_OK, *new_root_host (HOST memory) receives the index of the first
+ * node of the sorted list.  Synchronizes `stream`.
+ */
+pbit_status pbit_sort_list(const pbit_pool *pool, int32_t root, int64_t n, int32_t M, int32_t K,
+                           int32_t *new_root_host, const pbit_tune *tune, void *ws,
+                           size_t ws_bytes, void *stream);
+
+/*
+ * Sort `num_lists` independent lists sharing one pool in one segmented launch
+ * sequence.  d_offsets (DEVICE, num_lists+1 int64, non-decreasing, last <=
+ * pool_size): list i owns the nodes [d_offsets[i], d_offsets[i+1]) and must
+ * contain every one of them; d_roots (DEVICE, num_lists int32) are the heads
+ * (-1 for an empty list).  d_new_roots (DEVICE, num_lists int32) receives the
+ * sorted heads.  Nodes outside every range are never touched.  tune = NULL
+ * takes the autotuned choice for this size.  Synchronizes `stream`.
+ */
+pbit_status pbit_sort_lists_batched(const pbit_pool *pool, int32_t num_lists,
+                                    const int32_t *d_roots, const int64_t *d_offsets, int32_t M,
+                                    int32_t K, int32_t *d_new_roots, const pbit_tune *tune,
+                                    void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Number of kernel launches the last sort call on this thread enqueued (for
+ * benchmarks that report launches; 0 before any call).
+ */
+int64_t pbit_last_launch_count(void);
+
+/* ------------------------------------------------------------------ serving
+ * A server owns a device arena of at most mem_budget_bytes on `device` and a
+ * scheduler thread.  Requests are admitted while the workspace bytes of all
+ * admitted requests fit in the budget; admitted requests are batched as they
+ * arrive (continuous batching: requests that arrive while others run on the
+ * GPU are admitted as memory frees up and run concurrently on up to
+ * `streams` CUDA streams).  The caller owns each request's pool (device
+ * memory) and keeps it alive until poll returns something other than
+ * PBIT_EPENDING.
+ */
+typedef struct pbit_server pbit_server;
+
+pbit_status pbit_serve_create(pbit_server **out, size_t mem_budget_bytes, int32_t device,
+                              int32_t streams, int32_t max_batch);
+/* Queue one request; *ticket identifies it.  PBIT_EAGAIN if the request can
+ * never fit the budget; PBIT_EINVAL on bad arguments. */
+pbit_status pbit_serve_submit(pbit_server *s, const pbit_pool *pool, int32_t root, int64_t n,
+                              int32_t M, int32_t K, uint64_t *ticket);
+/* PBIT_EPENDING while queued or running; otherwise the request's final status,
+ * with *new_root set on PBIT_OK.  A finished ticket may be polled again. */
+pbit_status pbit_serve_poll(pbit_server *s, uint64_t ticket, int32_t *new_root);
+/* Block until the ticket finishes (or timeout_ms elapses: PBIT_EPENDING). */
+pbit_status pbit_serve_wait(pbit_server *s, uint64_t ticket, int32_t *new_root,
+                            int64_t timeout_ms);
+/* Server counters: [0] submitted, [1] completed, [2] batches launched,
+ * [3] max requests in one batch, [4] peak admitted bytes. */
+void pbit_serve_stats(pbit_server *s, int64_t *out5);
+void pbit_serve_destroy(pbit_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBIT_H */

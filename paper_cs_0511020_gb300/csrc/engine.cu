@@ -1,0 +1,369 @@
+// engine.cu -- host orchestration and the C ABI of include/pbit.h.
+//
+// One sort call = one stream-ordered sequence:
+//   memsets -> setup -> walk -> wyllie rounds -> validate + emit
+//   -> plan_init -> ceil(M/D) x [seg_stats, plan_pending, pass, plan]
+//   -> check -> finish -> relink -> status read-back.
+// The workspace is carved into fixed regions whose sizes depend only on the
+// pool size, the number of lists, the key width and the tune; no call
+// allocates device memory.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "engine.h"
+#include "pbit_internal.cuh"
+
+namespace pbit {
+
+static thread_local int64_t g_last_launches = 0;
+
+static inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return 148;
+    static std::mutex mu;
+    static std::unordered_map<int, int> cache;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end())
+        return it->second;
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        sms = 148;
+    cache[dev] = sms;
+    return sms;
+}
+
+bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out) {
+    Tune r;
+    r.digit_bits = digit_bits();
+    r.cutoff = finish_capacity();
+    r.log2S = 5;
+    if (t) {
+        if (t->digit_bits > 0 && t->digit_bits != digit_bits())
+            return false;
+        if (t->smem_cutoff > 0) {
+            if (t->smem_cutoff > finish_capacity())
+                return false;
+            r.cutoff = t->smem_cutoff;
+        }
+        if (t->ruler_stride > 0) {
+            int s = t->ruler_stride, l = 0;
+            while ((1 << l) < s)
+                ++l;
+            if ((1 << l) != s || l < 1 || l > 12)
+                return false;
+            r.log2S = l;
+        }
+    }
+    (void)pool_size;
+    (void)kb;
+    *out = r;
+    return true;
+}
+
+Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms) {
+    Sizes z;
+    z.ncap = ncap;
+    z.L = L;
+    z.kb = kb;
+    z.tune = t;
+    z.CH = 32;
+    const int64_t S = 1ll << t.log2S;
+    z.R0 = (ncap + S - 1) / S;
+    z.Rcap = z.R0 + L;
+    const int64_t walk_warps = (int64_t)sms * 8 * 8;
+    z.chunk_cap = (ncap + z.CH - 1) / z.CH + z.Rcap + 64 * walk_warps + 64;
+    z.seg_cap = ncap / (t.cutoff + 1) + 2;
+    const int64_t iters = (8 * kb + t.digit_bits - 1) / t.digit_bits;
+    z.fin_cap = L + (int64_t)(1 << t.digit_bits) * iters * z.seg_cap + 16;
+    z.tile_cap = ncap / pass_tile() + z.seg_cap + 2;
+    return z;
+}
+
+// Carve the workspace.  With ws == nullptr only the size is computed.
+size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> unsigned char * {
+        unsigned char *p = ws ? ws + off : nullptr;
+        off += up256(bytes);
+        return p;
+    };
+    auto zero = [&](void *p, int v, size_t bytes) {
+        if (ms && p)
+            ms->push_back(Memset{p, v, bytes});
+    };
+    Ctx x;
+    std::memset(&x, 0, sizeof x);
+    x.num_lists = z.L;
+    x.key_bytes = z.kb;
+    x.D = z.tune.digit_bits;
+    x.log2S = z.tune.log2S;
+    x.cutoff = z.tune.cutoff;
+    x.CH = z.CH;
+    x.ncap = z.ncap;
+    x.R0 = (int32_t)z.R0;
+    x.Rcap = (int32_t)z.Rcap;
+    x.chunk_cap = z.chunk_cap;
+    x.seg_cap = z.seg_cap;
+    x.fin_cap = z.fin_cap;
+    x.tile_cap = z.tile_cap;
+    const int bins = 1 << z.tune.digit_bits;
+
+    x.ctr = (Counters *)take(sizeof(Counters));
+    zero(x.ctr, 0, sizeof(Counters));
+    x.status = (int32_t *)take(64);
+    zero(x.status, 0, 64);
+    x.new_roots = (int32_t *)take(64);  // single-list result slot
+    x.desc = (ListDesc *)take(sizeof(ListDesc) * (size_t)z.L);
+    x.out_base = (int32_t *)take(4 * (size_t)(z.L + 1));
+    x.root_task = (int32_t *)take(4 * (size_t)z.L);
+    x.task_list = (int32_t *)take(4 * (size_t)z.Rcap);
+    x.task_len = (int32_t *)take(4 * (size_t)z.Rcap);
+    zero(x.task_len, 0, 4 * (size_t)z.Rcap);
+    x.task_succ = (int32_t *)take(4 * (size_t)z.Rcap);
+    zero(x.task_succ, 0xff, 4 * (size_t)z.Rcap);
+    for (int b = 0; b < 2; ++b)
+        x.wy[b] = (int64_t *)take(8 * (size_t)z.Rcap);
+    x.chunk_task = (int32_t *)take(4 * (size_t)z.chunk_cap);
+    zero(x.chunk_task, 0xff, 4 * (size_t)z.chunk_cap);
+    x.chunk_j0 = (int32_t *)take(4 * (size_t)z.chunk_cap);
+    x.chunk_data = (int32_t *)take(4 * (size_t)z.chunk_cap * z.CH);
+    for (int b = 0; b < 2; ++b)
+        x.keyb[b] = take((size_t)z.ncap * z.kb + 64);
+    for (int b = 0; b < 2; ++b)
+        x.idxb[b] = (int32_t *)take((size_t)z.ncap * 4 + 64);
+    x.F = (int32_t *)take((size_t)z.ncap * 4 + 64);
+    for (int b = 0; b < 2; ++b) {
+        x.act[b] = (Seg *)take(sizeof(Seg) * (size_t)z.seg_cap);
+        x.act_hist[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * bins);
+        x.act_tile_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
+        x.nh[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * bins * bins);
+        zero(x.nh[b], 0, 4 * (size_t)z.seg_cap * bins * bins);
+        x.band[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap * bins);
+        zero(x.band[b], 0xff, 8 * (size_t)z.seg_cap * bins);
+        x.bor[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap * bins);
+        zero(x.bor[b], 0, 8 * (size_t)z.seg_cap * bins);
+        x.pend[b] = (Seg *)take(sizeof(Seg) * (size_t)z.seg_cap);
+        x.pend_tile_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
+        x.phist[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * 16 * bins);
+        zero(x.phist[b], 0, 4 * (size_t)z.seg_cap * 16 * bins);
+        x.pand[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap);
+        zero(x.pand[b], 0xff, 8 * (size_t)z.seg_cap);
+        x.por[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap);
+        zero(x.por[b], 0, 8 * (size_t)z.seg_cap);
+    }
+    x.fin = (Fin *)take(sizeof(Fin) * (size_t)z.fin_cap);
+    x.lb = (unsigned long long *)take(8 * (size_t)z.tile_cap * bins);
+    zero(x.lb, 0, 8 * (size_t)z.tile_cap * bins);
+    if (c)
+        *c = x;
+    return off + 256;
+}
+
+static int ceil_log2(int64_t x) {
+    int r = 0;
+    while ((1ll << r) < x)
+        ++r;
+    return r;
+}
+
+// Enqueue the whole sort on stream s.  Returns PBIT_ECUDA if a launch failed.
+pbit_status enqueue_sort(const Ctx &c, const std::vector<Memset> &ms, int mode, const ListDesc *tmpl,
+                         const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s,
+                         int sms, int64_t *launches) {
+    int64_t n = 0;
+    for (const Memset &m : ms) {
+        if (cudaMemsetAsync(m.p, m.v, m.bytes, s) != cudaSuccess)
+            return PBIT_ECUDA;
+        ++n;
+    }
+    Ctx cc = c;
+    cc.M = M;
+    launch_setup(cc, d_offsets, d_roots, mode, tmpl, s, sms);
+    launch_walk(cc, s, sms);
+    const int rounds = ceil_log2(cc.Rcap) + 1;
+    launch_wyllie(cc, s, sms, rounds);
+    launch_validate_emit(cc, rounds & 1, s, sms);
+    launch_plan_init(cc, s);
+    n += 6 + rounds;
+    const int iters = (M + cc.D - 1) / cc.D;
+    for (int it = 0; it < iters; ++it)
+        launch_iteration(cc, it, s, sms);
+    n += iters * launches_per_iteration();
+    launch_check_done(cc, iters, s);
+    launch_finish_relink(cc, s, sms);
+    n += 4;
+    if (launches)
+        *launches = n;
+    if (cudaGetLastError() != cudaSuccess)
+        return PBIT_ECUDA;
+    return PBIT_OK;
+}
+
+pbit_status map_status(int st) {
+    if (st == 0)
+        return PBIT_OK;
+    if (st == kStOverflow)
+        return PBIT_ENOMEM;
+    if (st > 0 && st <= PBIT_EPENDING)
+        return (pbit_status)st;
+    return PBIT_ECUDA;
+}
+
+static bool check_pool(const pbit_pool *p, int M, int K) {
+    if (!p || !p->next || !p->key)
+        return false;
+    const int kb = p->key_type;
+    if (kb != 1 && kb != 2 && kb != 4 && kb != 8)
+        return false;
+    if (K < 1 || K > 16 || M < 1 || M > 8 * kb || M % K != 0)
+        return false;
+    if (p->pool_size < 0 || p->pool_size >= (1ll << 31))
+        return false;
+    if (p->next_stride_bytes < 4 || p->next_stride_bytes % 4 != 0)
+        return false;
+    if (p->key_stride_bytes < kb || p->key_stride_bytes % kb != 0)
+        return false;
+    if ((p->flags & (PBIT_SIGNED | PBIT_FLOAT)) && M != 8 * kb)
+        return false;
+    if ((p->flags & PBIT_FLOAT) && kb < 4)
+        return false;
+    if ((p->flags & PBIT_DOUBLY) && (!p->prev || p->prev_stride_bytes < 4 || p->prev_stride_bytes % 4 != 0))
+        return false;
+    if (p->flags & ~(PBIT_SIGNED | PBIT_DESCENDING | PBIT_DOUBLY | PBIT_FLOAT))
+        return false;
+    if ((reinterpret_cast<uintptr_t>(p->next) & 3) || (reinterpret_cast<uintptr_t>(p->key) & (kb - 1)))
+        return false;
+    return true;
+}
+
+static ListDesc pool_template(const pbit_pool *p) {
+    ListDesc t{};
+    t.next = p->next;
+    t.key = (const unsigned char *)p->key;
+    t.prev = p->prev;
+    t.next_stride = p->next_stride_bytes;
+    t.key_stride = p->key_stride_bytes;
+    t.prev_stride = p->prev_stride_bytes;
+    return t;
+}
+
+// Shared body of the single-list and batched calls (a pool with list ranges).
+static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
+                             const int64_t *d_offsets, int single_root, int64_t single_n, int M, int K,
+                             int32_t *d_new_roots, int32_t *host_root, const pbit_tune *tune, void *ws,
+                             size_t ws_bytes, cudaStream_t s) {
+    (void)K;
+    Tune t;
+    if (!resolve_tune(tune, pool->pool_size, pool->key_type, &t))
+        return PBIT_EINVAL;
+    const int sms = device_sms();
+    Sizes z = compute_sizes(pool->pool_size, num_lists, pool->key_type, t, sms);
+    Ctx c;
+    std::vector<Memset> ms;
+    size_t need = bind(z, (unsigned char *)ws, &c, &ms);
+    if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255))
+        return ws_bytes < need ? PBIT_ENOMEM : PBIT_EINVAL;
+    c.flags = pool->flags;
+    if (d_new_roots)
+        c.new_roots = d_new_roots;
+    ListDesc tmpl = pool_template(pool);
+    pbit_status rc;
+    if (d_offsets) {
+        rc = enqueue_sort(c, ms, 0, &tmpl, d_offsets, d_roots, M, s, sms, &g_last_launches);
+    } else {
+        // single list: its descriptor comes from the call arguments
+        ListDesc d = tmpl;
+        d.n = (int32_t)single_n;
+        d.root = single_root;
+        d.id_base = 0;
+        d.out_base = 0;
+        rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, &g_last_launches);
+    }
+    if (rc != PBIT_OK)
+        return rc;
+    static thread_local int32_t *hbuf = nullptr;
+    if (!hbuf && cudaMallocHost((void **)&hbuf, 64) != cudaSuccess)
+        return PBIT_ECUDA;
+    if (cudaMemcpyAsync(hbuf, c.status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PBIT_ECUDA;
+    if (host_root && cudaMemcpyAsync(hbuf + 1, c.new_roots, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PBIT_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return PBIT_ECUDA;
+    pbit_status st = map_status(hbuf[0]);
+    if (st == PBIT_OK && host_root)
+        *host_root = hbuf[1];
+    return st;
+}
+
+}  // namespace pbit
+
+using namespace pbit;
+
+extern "C" {
+
+const char *pbit_status_string(int status) {
+    switch (status) {
+    case PBIT_OK: return "ok";
+    case PBIT_EINVAL: return "invalid argument";
+    case PBIT_ENOMEM: return "workspace too small or capacity exceeded";
+    case PBIT_EBADLIST: return "malformed list (cycle, wrong length, index out of range or bad root)";
+    case PBIT_ETIMEOUT: return "a bounded device wait gave up";
+    case PBIT_ECUDA: return "CUDA runtime error";
+    case PBIT_EAGAIN: return "request not admitted";
+    case PBIT_EPENDING: return "request pending";
+    default: return "unknown status";
+    }
+}
+
+pbit_status pbit_workspace_size(int64_t pool_size, int32_t num_lists, int32_t key_type, const pbit_tune *tune,
+                                size_t *bytes) {
+    if (!bytes || pool_size < 0 || pool_size >= (1ll << 31) || num_lists < 1)
+        return PBIT_EINVAL;
+    if (key_type != 1 && key_type != 2 && key_type != 4 && key_type != 8)
+        return PBIT_EINVAL;
+    Tune t;
+    if (!resolve_tune(tune, pool_size, key_type, &t))
+        return PBIT_EINVAL;
+    Sizes z = compute_sizes(pool_size, num_lists, key_type, t, device_sms());
+    *bytes = bind(z, nullptr, nullptr, nullptr);
+    return PBIT_OK;
+}
+
+pbit_status pbit_sort_list(const pbit_pool *pool, int32_t root, int64_t n, int32_t M, int32_t K,
+                           int32_t *new_root_host, const pbit_tune *tune, void *ws, size_t ws_bytes,
+                           void *stream) {
+    if (!check_pool(pool, M, K) || !new_root_host)
+        return PBIT_EINVAL;
+    if (n != pool->pool_size)
+        return PBIT_EINVAL;
+    if (n == 0) {
+        if (root != -1)
+            return PBIT_EBADLIST;
+        *new_root_host = -1;
+        return PBIT_OK;
+    }
+    if (root < 0 || root >= n)
+        return PBIT_EBADLIST;
+    return sort_pool(pool, 1, nullptr, nullptr, root, n, M, K, nullptr, new_root_host, tune, ws, ws_bytes,
+                     (cudaStream_t)stream);
+}
+
+pbit_status pbit_sort_lists_batched(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
+                                    const int64_t *d_offsets, int32_t M, int32_t K, int32_t *d_new_roots,
+                                    const pbit_tune *tune, void *ws, size_t ws_bytes, void *stream) {
+    if (!check_pool(pool, M, K) || num_lists < 1 || !d_roots || !d_offsets || !d_new_roots)
+        return PBIT_EINVAL;
+    return sort_pool(pool, num_lists, d_roots, d_offsets, 0, 0, M, K, d_new_roots, nullptr, tune, ws, ws_bytes,
+                     (cudaStream_t)stream);
+}
+
+int64_t pbit_last_launch_count(void) { return g_last_launches; }
+
+}  // extern "C"

@@ -1,0 +1,40 @@
+// engine.h -- host-side pieces of the sort engine shared by the C ABI
+// (engine.cu) and the request server (serve.cu).
+#pragma once
+#include <vector>
+
+#include "pbit_internal.cuh"
+
+namespace pbit {
+
+struct Tune {
+    int digit_bits;
+    int cutoff;
+    int log2S;
+};
+
+struct Sizes {
+    int64_t ncap;
+    int32_t L;
+    int kb;
+    Tune tune;
+    int CH;
+    int64_t R0, Rcap, chunk_cap, seg_cap, fin_cap, tile_cap;
+};
+
+struct Memset {
+    void *p;
+    int v;
+    size_t bytes;
+};
+
+int device_sms();
+bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out);
+Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms);
+size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms);
+pbit_status enqueue_sort(const Ctx &c, const std::vector<Memset> &ms, int mode, const ListDesc *tmpl,
+                         const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s, int sms,
+                         int64_t *launches);
+pbit_status map_status(int st);
+
+}  // namespace pbit

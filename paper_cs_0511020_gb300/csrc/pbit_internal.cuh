@@ -1,0 +1,288 @@
+// pbit_internal.cuh -- device-side layout and helpers shared by the kernels of
+// the GB300 Pbit list sort.  Host orchestration is in engine.cu.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pbit.h"
+
+namespace pbit {
+
+constexpr int kWarp = 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Internal status values beyond the ABI's pbit_status (never returned).
+constexpr int kStOverflow = 100;  // a capacity computed on the host was exceeded
+
+// ----------------------------------------------------------------- layouts
+// One list as the kernels see it.  Node ids are "local" (0..n-1); the pool
+// index of local node v is id_base + v; its sorted position lies in
+// [out_base, out_base + n) of the order buffers.
+struct ListDesc {
+    int32_t *next;
+    const unsigned char *key;
+    int32_t *prev;
+    int64_t next_stride;  // bytes
+    int64_t key_stride;   // bytes
+    int64_t prev_stride;  // bytes
+    int32_t n;
+    int32_t root;      // local root, -1 for an empty list
+    int32_t id_base;
+    int32_t out_base;
+};
+
+// A contiguous run of the order buffers that still has to be sorted on the
+// key bits [0, hi); an active segment is split in the next pass on [lo, hi).
+struct Seg {
+    int32_t start;
+    int32_t len;
+    int32_t lo;
+    int32_t hi;
+};
+
+// A finished-or-small run: mode 0 = copy the node ids to the final buffer,
+// mode 1 = sort on bits [0, hi) in shared memory first.  buf = order buffer
+// parity that holds it.
+struct Fin {
+    int32_t start;
+    int32_t len;
+    int32_t hi;
+    int32_t mode_buf;  // (mode << 8) | buf
+};
+
+constexpr int kMaxIters = 64;
+
+struct Counters {
+    int32_t n_virt;            // total nodes over all lists
+    int32_t chunk_next;        // bump allocator of ranking chunks
+    int32_t fin_count;
+    int32_t fin_ctr;           // work counter of the finish kernel
+    int32_t act_count[2];
+    int32_t pend_count[2];
+    int32_t num_tiles[2];
+    int32_t stat_tiles[2];
+    int32_t tile_ctr[kMaxIters];
+    int32_t stat_ctr[kMaxIters];
+    int32_t pad[16];
+};
+
+// Everything a kernel needs, passed by value.
+struct Ctx {
+    // problem
+    int32_t num_lists;
+    int32_t key_bytes;
+    int32_t M;
+    int32_t D;          // GPU digit width per pass (4)
+    int32_t log2S;      // ruler stride S = 1 << log2S
+    int32_t cutoff;     // buckets <= cutoff are finished in shared memory
+    int32_t flags;      // PBIT_SIGNED | PBIT_DESCENDING | PBIT_FLOAT | PBIT_DOUBLY
+    int32_t CH;         // ranking chunk entries
+    int64_t ncap;       // capacity of the order buffers (pool size)
+    int32_t R0;         // hash-ruler tasks
+    int32_t Rcap;       // R0 + num_lists
+    int64_t chunk_cap;
+    int64_t seg_cap;    // active/pending segments per pass
+    int64_t fin_cap;
+    int64_t tile_cap;   // tiles per pass
+    // arrays
+    ListDesc *desc;
+    int32_t *out_base;  // num_lists + 1 prefix (device copy of desc[].out_base)
+    Counters *ctr;
+    int32_t *status;
+    int32_t *root_task;
+    int32_t *task_list;
+    int32_t *task_len;
+    int32_t *task_succ;
+    int64_t *wy[2];     // packed (succ << 32) | suffix length, ping-pong
+    int32_t *chunk_task;
+    int32_t *chunk_j0;
+    int32_t *chunk_data;
+    unsigned char *keyb[2];
+    int32_t *idxb[2];
+    int32_t *F;
+    Seg *act[2];
+    uint32_t *act_hist[2];      // seg_cap x 16 : histogram of the pass window
+    int32_t *act_tile_base[2];  // seg_cap + 1
+    uint32_t *nh[2];            // seg_cap x 16 x 16 : next-window histogram per bucket
+    unsigned long long *band[2];// seg_cap x 16
+    unsigned long long *bor[2];
+    Seg *pend[2];
+    int32_t *pend_tile_base[2];
+    uint32_t *phist[2];         // seg_cap x 16 windows x 16 bins
+    unsigned long long *pand[2];
+    unsigned long long *por[2];
+    Fin *fin;
+    unsigned long long *lb;     // tile_cap x 16 look-back words
+    int32_t *new_roots;
+};
+
+// ----------------------------------------------------------------- helpers
+__device__ __forceinline__ void set_status(int32_t *st, int code) { atomicCAS(st, 0, code); }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    // MurmurHash3 finaliser (public domain, A. Appleby)
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Position of the hash ruler of ruler block j (virtual positions [jS, jS+S)).
+__device__ __forceinline__ int32_t ruler_of_block(int32_t j, int32_t log2S, int32_t n_virt) {
+    int32_t base = j << log2S;
+    int32_t blk = min(1 << log2S, n_virt - base);
+    uint32_t h = fmix32((uint32_t)j * 0x9E3779B1u + 0x0511020u);
+    int32_t off = (blk == (1 << log2S)) ? (int32_t)(h & ((1u << log2S) - 1)) : (int32_t)(h % (uint32_t)blk);
+    return base + off;
+}
+
+__device__ __forceinline__ bool is_ruler(int32_t p, int32_t log2S, int32_t n_virt) {
+    return ruler_of_block(p >> log2S, log2S, n_virt) == p;
+}
+
+// largest i in [0, n) with a[i] <= x (a non-decreasing, a[0] <= x)
+__device__ __forceinline__ int32_t upper_index(const int32_t *a, int32_t n, int32_t x) {
+    int32_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int32_t mid = (lo + hi + 1) >> 1;
+        if (__ldg(a + mid) <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename KeyT>
+__device__ __forceinline__ KeyT load_key_raw(const unsigned char *p) {
+    return *reinterpret_cast<const KeyT *>(p);
+}
+
+// Order-preserving transform of a key into the unsigned sort key of M bits.
+template <typename KeyT>
+__device__ __forceinline__ KeyT sort_key(KeyT k, int flags, int M) {
+    constexpr int W = 8 * sizeof(KeyT);
+    const KeyT sign = (KeyT)((KeyT)1 << (W - 1));
+    if (flags & PBIT_FLOAT)
+        k = (k & sign) ? (KeyT)~k : (KeyT)(k ^ sign);
+    else if (flags & PBIT_SIGNED)
+        k = (KeyT)(k ^ sign);
+    if (flags & PBIT_DESCENDING)
+        k = (KeyT)~k;
+    if (M < W)
+        k = (KeyT)(k & (KeyT)(((KeyT)1 << M) - 1));
+    return k;
+}
+
+// ------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared (the TMA engine), completing on `bar`.
+// dst, src and bytes must all be multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every device-side wait gives up after this long and reports PBIT_ETIMEOUT.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Bounded wait on an mbarrier phase; false if the time or iteration limit
+// was reached.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit) {
+    const uint64_t t0 = globaltimer_ns();
+    for (long long i = 0; i < limit; ++i) {
+        if (mbar_try_wait(bar, parity))
+            return true;
+        if ((i & 255) == 255 && globaltimer_ns() - t0 > kWaitLimitNs)
+            return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Decoupled look-back words: [63:56] pass epoch, [55:54] state, [53:0] count.
+constexpr unsigned long long kLbAgg = 1ull;
+constexpr unsigned long long kLbIncl = 2ull;
+__device__ __forceinline__ unsigned long long lb_pack(uint32_t epoch, unsigned long long state,
+                                                      unsigned long long count) {
+    return ((unsigned long long)(epoch & 0xff) << 56) | (state << 54) | (count & ((1ull << 54) - 1));
+}
+
+// ---------------------------------------------------------- launch helpers
+struct Launch {
+    int sms;
+};
+
+// kernel entry points (defined in rank.cu / msd.cu / finish.cu)
+void launch_setup(const Ctx &c, const int64_t *d_offsets, const int32_t *d_roots, int mode,
+                  const ListDesc *host_desc_tmpl, cudaStream_t s, int sms);
+void launch_walk(const Ctx &c, cudaStream_t s, int sms);
+void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds);
+void launch_validate_emit(const Ctx &c, int final_wy, cudaStream_t s, int sms);
+void launch_plan_init(const Ctx &c, cudaStream_t s);
+void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms);
+void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms);
+void launch_check_done(const Ctx &c, int iters, cudaStream_t s);
+int64_t launches_per_iteration();
+int finish_capacity();
+int pass_tile();
+int stat_tile();
+int digit_bits();
+
+}  // namespace pbit

@@ -1,0 +1,175 @@
+"""ctypes binding of libpbit.so (include/pbit.h) taking torch device tensors.
+
+Argument marshalling only: every step of the sort runs in the library's CUDA
+kernels.  If the library is missing this module raises instead of falling
+back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpbit.so")
+
+OK, EINVAL, ENOMEM, EBADLIST, ETIMEOUT, ECUDA, EAGAIN, EPENDING = range(8)
+SIGNED, DESCENDING, DOUBLY, FLOAT = 1, 2, 4, 8
+
+EXPORTS = ("pbit_status_string", "pbit_workspace_size", "pbit_sort_list", "pbit_sort_lists_batched",
+           "pbit_last_launch_count", "pbit_serve_create", "pbit_serve_submit", "pbit_serve_poll",
+           "pbit_serve_wait", "pbit_serve_stats", "pbit_serve_destroy")
+
+
+class PbitError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: pbit status {status} ({status_string(status)})")
+
+
+class Pool(ctypes.Structure):
+    _fields_ = [("next", ctypes.c_void_p), ("next_stride_bytes", ctypes.c_int64),
+                ("key", ctypes.c_void_p), ("key_stride_bytes", ctypes.c_int64),
+                ("key_type", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("pool_size", ctypes.c_int64), ("prev", ctypes.c_void_p),
+                ("prev_stride_bytes", ctypes.c_int64)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("digit_bits", ctypes.c_int32), ("smem_cutoff", ctypes.c_int32),
+                ("ruler_stride", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.pbit_status_string.restype = ctypes.c_char_p
+        L.pbit_status_string.argtypes = [ctypes.c_int]
+        L.pbit_workspace_size.restype = ctypes.c_int
+        L.pbit_workspace_size.argtypes = [i64, i32, i32, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.pbit_sort_list.restype = ctypes.c_int
+        L.pbit_sort_list.argtypes = [vp, i32, i64, i32, i32, ctypes.POINTER(i32), vp, vp,
+                                     ctypes.c_size_t, vp]
+        L.pbit_sort_lists_batched.restype = ctypes.c_int
+        L.pbit_sort_lists_batched.argtypes = [vp, i32, vp, vp, i32, i32, vp, vp, vp,
+                                              ctypes.c_size_t, vp]
+        L.pbit_last_launch_count.restype = i64
+        L.pbit_last_launch_count.argtypes = []
+        _lib = L
+    return _lib
+
+
+def status_string(st: int) -> str:
+    return lib().pbit_status_string(int(st)).decode()
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _tune_ptr(tune):
+    if tune is None:
+        return None, None
+    if isinstance(tune, dict):
+        tune = Tune(tune.get("digit_bits", 0), tune.get("smem_cutoff", 0), tune.get("ruler_stride", 0), 0)
+    return tune, ctypes.addressof(tune)
+
+
+def make_pool(next_t: torch.Tensor, key_t: torch.Tensor, flags: int = 0,
+              prev_t: torch.Tensor | None = None) -> Pool:
+    """SoA pool: next_t int32[n] and key_t of 1/2/4/8-byte elements, both CUDA."""
+    assert next_t.is_cuda and key_t.is_cuda and next_t.dtype == torch.int32
+    assert next_t.is_contiguous() and key_t.is_contiguous() and next_t.numel() == key_t.numel()
+    kb = key_t.element_size()
+    p = Pool(next_t.data_ptr(), 4, key_t.data_ptr(), kb, kb, flags, next_t.numel(), 0, 0)
+    if prev_t is not None:
+        assert prev_t.dtype == torch.int32 and prev_t.is_contiguous() and prev_t.numel() == next_t.numel()
+        p.prev, p.prev_stride_bytes = prev_t.data_ptr(), 4
+        p.flags |= DOUBLY
+    return p
+
+
+def make_pool_aos(nodes_t: torch.Tensor, flags: int = 0) -> Pool:
+    """AoS pool of 8-byte nodes {int32 next; uint32 key}: an int32 tensor [n, 2]."""
+    assert nodes_t.is_cuda and nodes_t.dtype == torch.int32 and nodes_t.dim() == 2 and nodes_t.shape[1] == 2
+    assert nodes_t.is_contiguous()
+    base = nodes_t.data_ptr()
+    return Pool(base, 8, base + 4, 8, 4, flags, nodes_t.shape[0], 0, 0)
+
+
+def workspace_size(pool_size: int, num_lists: int, key_bytes: int, tune=None) -> int:
+    out = ctypes.c_size_t(0)
+    tune, tp = _tune_ptr(tune)
+    st = lib().pbit_workspace_size(int(pool_size), int(num_lists), int(key_bytes), tp, ctypes.byref(out))
+    if st != OK:
+        raise PbitError(st, "pbit_workspace_size")
+    return int(out.value)
+
+
+def alloc_workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Device workspace (torch's caching allocator returns >= 512-byte alignment)."""
+    ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+def sort_pool_list(pool: Pool, root: int, n: int, M: int, K: int = 4, ws: torch.Tensor | None = None,
+                   tune=None, stream=None, check: bool = True):
+    """pbit_sort_list on a prepared Pool; returns (status, new_root)."""
+    if ws is None:
+        ws = alloc_workspace(workspace_size(pool.pool_size, 1, pool.key_type, tune))
+    tune, tp = _tune_ptr(tune)
+    nr = ctypes.c_int32(-7)
+    st = lib().pbit_sort_list(ctypes.addressof(pool), int(root), int(n), int(M), int(K), ctypes.byref(nr), tp,
+                              ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    if check and st != OK:
+        raise PbitError(st, "pbit_sort_list")
+    return st, int(nr.value)
+
+
+def sort_list(next_t: torch.Tensor, key_t: torch.Tensor, root: int, M: int | None = None, K: int = 4,
+              flags: int = 0, prev_t=None, ws=None, tune=None, stream=None) -> int:
+    """Sort the list in place (next_t relinked); returns the new root."""
+    pool = make_pool(next_t, key_t, flags, prev_t)
+    M = 8 * key_t.element_size() if M is None else M
+    return sort_pool_list(pool, root, next_t.numel(), M, K, ws, tune, stream)[1]
+
+
+def sort_pool_batched(pool: Pool, roots_t: torch.Tensor, offsets_t: torch.Tensor, M: int, K: int = 4,
+                      new_roots_t: torch.Tensor | None = None, ws=None, tune=None, stream=None,
+                      check: bool = True):
+    assert roots_t.dtype == torch.int32 and offsets_t.dtype == torch.int64
+    L = roots_t.numel()
+    assert offsets_t.numel() == L + 1
+    if new_roots_t is None:
+        new_roots_t = torch.empty(L, dtype=torch.int32, device=roots_t.device)
+    if ws is None:
+        ws = alloc_workspace(workspace_size(pool.pool_size, L, pool.key_type, tune))
+    tune, tp = _tune_ptr(tune)
+    st = lib().pbit_sort_lists_batched(ctypes.addressof(pool), L, roots_t.data_ptr(), offsets_t.data_ptr(),
+                                       int(M), int(K), new_roots_t.data_ptr(), tp, ws.data_ptr(), ws.numel(),
+                                       _stream_handle(stream))
+    if check and st != OK:
+        raise PbitError(st, "pbit_sort_lists_batched")
+    return st, new_roots_t
+
+
+def sort_lists_batched(next_t, key_t, roots_t, offsets_t, M=None, K=4, flags=0, ws=None, tune=None,
+                       stream=None):
+    pool = make_pool(next_t, key_t, flags)
+    M = 8 * key_t.element_size() if M is None else M
+    return sort_pool_batched(pool, roots_t, offsets_t, M, K, None, ws, tune, stream)[1]
+
+
+def last_launch_count() -> int:
+    return int(lib().pbit_last_launch_count())

@@ -1,0 +1,240 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle, bit-exact
+on next[] and the root, on seeded inputs of the workloads' shapes."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_cs_0511020_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+_NP = {1: np.uint8, 2: np.uint16, 4: np.uint32, 8: np.uint64}
+_TORCH_VIEW = {1: np.uint8, 2: np.int16, 4: np.int32, 8: np.int64}
+
+
+@pytest.fixture(scope="module")
+def pb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_cs_0511020_gb300 import pbit
+    pbit.lib()
+    return pbit
+
+
+def _dev_key(key):
+    return torch.from_numpy(np.ascontiguousarray(key).view(_TORCH_VIEW[key.itemsize])).cuda()
+
+
+def _gpu_sort(pb, nxt, key, root, M, K=4, flags=0, tune=None):
+    d_next = torch.from_numpy(nxt.copy()).cuda()
+    d_key = _dev_key(key)
+    pool = pb.make_pool(d_next, d_key, flags)
+    st, r = pb.sort_pool_list(pool, root, nxt.size, M, K, tune=tune, check=False)
+    torch.cuda.synchronize()
+    return st, d_next.cpu().numpy(), r
+
+
+def _check_vs_oracle(pb, nxt, key, root, M, K=4, tune=None):
+    st, got, r = _gpu_sort(pb, nxt, key, root, M, K, tune=tune)
+    assert st == pb.OK, pb.status_string(st)
+    if (M // K) % 2 == 0:
+        want, wr, _ = O.pbit_sort(nxt, key, root, M, K)
+    else:  # odd number of levels: the literal code is not stable; use the definition
+        want, wr = O.stable_sort_definition(nxt, key, root, M)
+    assert r == wr
+    assert (got == want).all(), f"{(got != want).sum()} next[] entries differ"
+
+
+def test_worked_example(pb):
+    keys = np.array([21, 3, 209, 14, 156, 47, 3, 214], dtype=np.uint8)
+    nxt, root = I.list_from_order(np.arange(8))
+    st, got, r = _gpu_sort(pb, nxt, keys, root, 8, 4)
+    assert st == pb.OK
+    order = O.list_order(got, r)
+    assert keys[order].tolist() == [3, 3, 14, 21, 47, 156, 209, 214]
+    assert [v for v in order if keys[v] == 3] == [1, 6]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 15, 16, 17, 31, 32, 33, 255, 256, 257, 4095, 4096, 4097,
+                               8191, 8192, 8193, 65535, 65537, 300001])
+def test_sizes_u32(pb, n):
+    nxt, root = I.random_list(n, 1000 + n)
+    key = I.uniform_keys(n, 4, 2000 + n)
+    key[::3] = key[0]
+    _check_vs_oracle(pb, nxt, key, root, 32)
+
+
+@pytest.mark.parametrize("kb", [1, 2, 4, 8])
+@pytest.mark.parametrize("n", [5000, 200003])
+def test_key_types(pb, kb, n):
+    nxt, root = I.random_list(n, 3000 + n + kb)
+    key = I.uniform_keys(n, kb, 4000 + n + kb)
+    _check_vs_oracle(pb, nxt, key, root, 8 * kb)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8, 16])
+def test_K_independent(pb, K):
+    n = 100000
+    nxt, root = I.random_list(n, 51)
+    key = I.uniform_keys(n, 4, 52) & np.uint32(0xFFF0FFFF)
+    _check_vs_oracle(pb, nxt, key, root, 32, K)
+
+
+def test_M_below_width(pb):
+    n = 70000
+    nxt, root = I.random_list(n, 61)
+    key = I.uniform_keys(n, 8, 62)
+    _check_vs_oracle(pb, nxt, key, root, 40, 4)
+    _check_vs_oracle(pb, nxt, key, root, 12, 4)
+
+
+def test_push_built_and_special(pb):
+    n = 150000
+    nxt, root = I.push_built_list(n)
+    key = I.uniform_keys(n, 4, 71)
+    _check_vs_oracle(pb, nxt, key, root, 32)
+    # all equal: unchanged
+    nxt, root = I.random_list(n, 72)
+    st, got, r = _gpu_sort(pb, nxt, np.full(n, 7, np.uint32), root, 32)
+    assert st == pb.OK and r == root and (got == nxt).all()
+    # strictly decreasing along the list: reversed
+    order = O.list_order(nxt, root)
+    key = np.empty(n, np.uint32)
+    key[order] = np.arange(n, 0, -1, dtype=np.uint32)
+    st, got, r = _gpu_sort(pb, nxt, key, root, 32)
+    assert st == pb.OK and O.list_order(got, r).tolist() == order[::-1].tolist()
+
+
+def test_skewed_u64_and_u8(pb):
+    n = 1 << 20
+    nxt, root = I.random_list(n, 81)
+    _check_vs_oracle(pb, nxt, I.zipf_u64_keys(n, 82), root, 64)
+    nxt, root = I.random_list(n, 83)
+    _check_vs_oracle(pb, nxt, I.uniform_keys(n, 1, 84), root, 8)
+
+
+def test_aos_pool(pb):
+    n = 1 << 20
+    nxt, root = I.random_list(n, 91)
+    key = I.uniform_keys(n, 4, 92)
+    nodes = torch.from_numpy(I.aos_pack(nxt, key)).cuda()
+    pool = pb.make_pool_aos(nodes)
+    st, r = pb.sort_pool_list(pool, root, n, 32, 4, check=False)
+    assert st == pb.OK
+    got = nodes[:, 0].cpu().numpy()
+    want, wr, _ = O.pbit_sort(nxt, key, root, 32, 4)
+    assert r == wr and (got == want).all()
+    assert (nodes[:, 1].cpu().numpy().view(np.uint32) == key).all()
+
+
+def test_batched(pb):
+    lens = I.log_uniform_lengths(300, 4, 17, 101, 16, 1 << 17)
+    lens[5] = 0
+    lens[6] = 1
+    nxt, key, roots, off = I.batched_pool(lens, 4, 102)
+    roots[5] = -1
+    d_next = torch.from_numpy(nxt.copy()).cuda()
+    nr = pb.sort_lists_batched(d_next, _dev_key(key), torch.from_numpy(roots).cuda(),
+                               torch.from_numpy(off).cuda(), M=32, K=4)
+    got = d_next.cpu().numpy()
+    nr = nr.cpu().numpy()
+    for i in range(lens.size):
+        a, b = off[i], off[i + 1]
+        if b == a:
+            assert nr[i] == -1
+            continue
+        sub_next = nxt[a:b] - np.where(nxt[a:b] >= 0, a, 0)
+        want, wr, _ = O.pbit_sort(sub_next.astype(np.int32), key[a:b], roots[i] - a, 32, 4)
+        want = np.where(want >= 0, want + a, -1)
+        assert nr[i] == wr + a
+        assert (got[a:b] == want).all(), f"list {i}"
+
+
+@pytest.mark.parametrize("case", ["cycle", "range", "short", "root"])
+def test_malformed_untouched(pb, case):
+    n = 50000
+    nxt, root = I.random_list(n, 111)
+    key = I.uniform_keys(n, 4, 112)
+    bad = nxt.copy()
+    order = O.list_order(nxt, root)
+    if case == "cycle":
+        bad[order[-1]] = order[n // 2]
+    elif case == "range":
+        bad[order[100]] = n + 5
+    elif case == "short":
+        bad[order[n - 10]] = -1
+    else:
+        root = n + 3
+    d_next = torch.from_numpy(bad.copy()).cuda()
+    pool = pb.make_pool(d_next, _dev_key(key))
+    st, _ = pb.sort_pool_list(pool, root, n, 32, 4, check=False)
+    assert st == pb.EBADLIST
+    assert (d_next.cpu().numpy() == bad).all()
+
+
+def test_bad_arguments(pb):
+    n = 100
+    nxt, root = I.random_list(n, 121)
+    d_next = torch.from_numpy(nxt).cuda()
+    pool = pb.make_pool(d_next, _dev_key(I.uniform_keys(n, 4, 122)))
+    assert pb.sort_pool_list(pool, root, n, 32, 5, check=False)[0] == pb.EINVAL
+    assert pb.sort_pool_list(pool, root, n, 33, 1, check=False)[0] == pb.EINVAL
+    assert pb.sort_pool_list(pool, root, n - 1, 32, 4, check=False)[0] == pb.EINVAL
+
+
+@pytest.mark.parametrize("flags", ["signed", "descending", "signed_desc", "float"])
+def test_signed_descending_float(pb, flags):
+    n = 120000
+    nxt, root = I.random_list(n, 131)
+    if flags == "float":
+        vals = I.rng(132).standard_normal(n).astype(np.float32)
+        vals[::11] = 0.0
+        vals[1::97] = -0.0
+        key = vals.view(np.uint32)
+        f = pb.FLOAT
+    else:
+        key = I.uniform_keys(n, 4, 133)
+        key[::4] = key[1]
+        f = {"signed": pb.SIGNED, "descending": pb.DESCENDING,
+             "signed_desc": pb.SIGNED | pb.DESCENDING}[flags]
+    st, got, r = _gpu_sort(pb, nxt, key, root, 32, 4, flags=f)
+    assert st == pb.OK
+    if flags == "float":
+        order_in = O.list_order(nxt, root)
+        v = vals[order_in]
+        # total order of the bit transform: -0.0 sorts before +0.0
+        perm = np.lexsort((np.arange(n), np.signbit(v) == False, v))  # noqa: E712
+        want, wr = O.relink(nxt, order_in[perm])
+    else:
+        want, wr = O.stable_sort_definition(nxt, key, root, 32, signed="signed" in flags,
+                                            descending="desc" in flags)
+    assert r == wr and (got == want).all()
+
+
+def test_doubly_linked(pb):
+    n = 90000
+    nxt, root = I.random_list(n, 141)
+    key = I.uniform_keys(n, 2, 142)
+    prev = np.full(n, -1, np.int32)
+    order = O.list_order(nxt, root)
+    prev[order[1:]] = order[:-1]
+    d_next = torch.from_numpy(nxt.copy()).cuda()
+    d_prev = torch.from_numpy(prev.copy()).cuda()
+    r = pb.sort_list(d_next, _dev_key(key), root, M=16, K=4, prev_t=d_prev)
+    got = d_next.cpu().numpy()
+    want, wr, _ = O.pbit_sort(nxt, key, root, 16, 4)
+    assert r == wr and (got == want).all()
+    out = O.list_order(got, r)
+    gp = d_prev.cpu().numpy()
+    assert gp[out[0]] == -1 and (gp[out[1:]] == out[:-1]).all()
+
+
+def test_tune_variants(pb):
+    n = 400000
+    nxt, root = I.random_list(n, 151)
+    key = I.uniform_keys(n, 4, 152)
+    for tune in ({"smem_cutoff": 1024}, {"ruler_stride": 8}, {"ruler_stride": 256},
+                 {"smem_cutoff": 256, "ruler_stride": 64}):
+        _check_vs_oracle(pb, nxt, key, root, 32, tune=tune)
