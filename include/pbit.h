@@ -119,10 +119,41 @@ pbit_status pbit_sort_lists_batched(const pbit_pool *pool, int32_t num_lists,
                                     void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Sort ONE list whose pool lives in HOST memory (pageable or pinned): the
+ * pool is copied to the device part of the workspace, sorted there, and
+ * next[] (and prev[] with PBIT_DOUBLY) copied back; key[] is only read.
+ * Same contract as pbit_sort_list otherwise; host_pool's pointers are host
+ * pointers.  The workspace (device) must hold pbit_workspace_size_host()
+ * bytes.  Synchronizes `stream`.
+ */
+pbit_status pbit_workspace_size_host(const pbit_pool *host_pool, const pbit_tune *tune, size_t *bytes);
+pbit_status pbit_sort_list_host(const pbit_pool *host_pool, int32_t root, int64_t n, int32_t M, int32_t K,
+                                int32_t *new_root_host, const pbit_tune *tune, void *ws, size_t ws_bytes,
+                                void *stream);
+
+/*
  * Number of kernel launches the last sort call on this thread enqueued (for
  * benchmarks that report launches; 0 before any call).
  */
 int64_t pbit_last_launch_count(void);
+
+/*
+ * Per-kernel device timing (instrumentation; not part of the method).  While
+ * enabled on a thread, every sort call on that thread records a CUDA event
+ * after each kernel on its stream; pbit_profile_read() then returns, for the
+ * last call, one entry per kernel kind: launches, summed device time in ms
+ * (time between consecutive events) and the algorithmic bytes that kind of
+ * kernel must move (reads + writes of its inputs and outputs).  Returns the
+ * number of entries written, or -1 on a CUDA error.
+ */
+typedef struct {
+    char name[24];
+    int32_t launches;
+    double ms;
+    double bytes;
+} pbit_kernel_stat;
+void pbit_profile_enable(int32_t on);
+int32_t pbit_profile_read(pbit_kernel_stat *out, int32_t max);
 
 /* ------------------------------------------------------------------ serving
  * A server owns a device arena of at most mem_budget_bytes on `device` and a

@@ -19,6 +19,52 @@ namespace pbit {
 
 static thread_local int64_t g_last_launches = 0;
 
+// ------------------------------------------------------------ profiling
+// When enabled, every launch site records an event after its kernel; the
+// time between consecutive events is charged to the kernel named there.
+struct ProfState {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<std::pair<const char *, cudaEvent_t>> marks;
+    cudaEvent_t start = nullptr;
+    Counters ctr;
+    bool have_ctr = false;
+    int64_t n = 0, rcap = 0, rounds = 0;
+    int kb = 4;
+    bool blocked_relink = false;
+};
+static thread_local ProfState g_prof;
+
+static cudaEvent_t prof_event() {
+    if (g_prof.used == g_prof.pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess)
+            return nullptr;
+        g_prof.pool.push_back(e);
+    }
+    return g_prof.pool[g_prof.used++];
+}
+
+void prof_mark(const char *name, cudaStream_t s) {
+    if (!g_prof.on)
+        return;
+    cudaEvent_t e = prof_event();
+    if (e && cudaEventRecord(e, s) == cudaSuccess)
+        g_prof.marks.emplace_back(name, e);
+}
+
+static void prof_begin(cudaStream_t s) {
+    if (!g_prof.on)
+        return;
+    g_prof.used = 0;
+    g_prof.marks.clear();
+    g_prof.have_ctr = false;
+    g_prof.start = prof_event();
+    if (g_prof.start)
+        cudaEventRecord(g_prof.start, s);
+}
+
 static inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 int device_sms() {
@@ -133,6 +179,7 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms) 
     zero(x.chunk_task, 0xff, 4 * (size_t)z.chunk_cap);
     x.chunk_j0 = (int32_t *)take(4 * (size_t)z.chunk_cap);
     x.chunk_data = (int32_t *)take(4 * (size_t)z.chunk_cap * z.CH);
+    x.chunk_key = take((size_t)z.kb * z.chunk_cap * z.CH);
     for (int b = 0; b < 2; ++b)
         x.keyb[b] = take((size_t)z.ncap * z.kb + 64);
     for (int b = 0; b < 2; ++b)
@@ -150,16 +197,19 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms) 
         zero(x.bor[b], 0, 8 * (size_t)z.seg_cap * bins);
         x.pend[b] = (Seg *)take(sizeof(Seg) * (size_t)z.seg_cap);
         x.pend_tile_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
-        x.phist[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * 16 * bins);
-        zero(x.phist[b], 0, 4 * (size_t)z.seg_cap * 16 * bins);
+        x.phist[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * bins);
+        zero(x.phist[b], 0, 4 * (size_t)z.seg_cap * bins);
         x.pand[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap);
         zero(x.pand[b], 0xff, 8 * (size_t)z.seg_cap);
         x.por[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap);
         zero(x.por[b], 0, 8 * (size_t)z.seg_cap);
     }
+    x.plan_cnt = (int4 *)take(sizeof(int4) * (size_t)z.seg_cap);
     x.fin = (Fin *)take(sizeof(Fin) * (size_t)z.fin_cap);
     x.lb = (unsigned long long *)take(8 * (size_t)z.tile_cap * bins);
     zero(x.lb, 0, 8 * (size_t)z.tile_cap * bins);
+    x.rel_cursor = (int32_t *)take(4 * (size_t)relink_max_buckets());
+    zero(x.rel_cursor, 0, 4 * (size_t)relink_max_buckets());
     if (c)
         *c = x;
     return off + 256;
@@ -176,12 +226,13 @@ static int ceil_log2(int64_t x) {
 pbit_status enqueue_sort(const Ctx &c, const std::vector<Memset> &ms, int mode, const ListDesc *tmpl,
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s,
                          int sms, int64_t *launches) {
-    int64_t n = 0;
+    int64_t n = 0;  // kernel launches
+    prof_begin(s);
     for (const Memset &m : ms) {
         if (cudaMemsetAsync(m.p, m.v, m.bytes, s) != cudaSuccess)
             return PBIT_ECUDA;
-        ++n;
     }
+    prof_mark("memset", s);
     Ctx cc = c;
     cc.M = M;
     launch_setup(cc, d_offsets, d_roots, mode, tmpl, s, sms);
@@ -190,7 +241,7 @@ pbit_status enqueue_sort(const Ctx &c, const std::vector<Memset> &ms, int mode, 
     launch_wyllie(cc, s, sms, rounds);
     launch_validate_emit(cc, rounds & 1, s, sms);
     launch_plan_init(cc, s);
-    n += 6 + rounds;
+    n += 7 + rounds;
     const int iters = (M + cc.D - 1) / cc.D;
     for (int it = 0; it < iters; ++it)
         launch_iteration(cc, it, s, sms);
@@ -198,6 +249,12 @@ pbit_status enqueue_sort(const Ctx &c, const std::vector<Memset> &ms, int mode, 
     launch_check_done(cc, iters, s);
     launch_finish_relink(cc, s, sms);
     n += 4;
+    if (g_prof.on) {
+        g_prof.rcap = cc.Rcap;
+        g_prof.rounds = rounds;
+        g_prof.kb = cc.key_bytes;
+        g_prof.blocked_relink = relink_blocked(cc);
+    }
     if (launches)
         *launches = n;
     if (cudaGetLastError() != cudaSuccess)
@@ -253,12 +310,11 @@ static ListDesc pool_template(const pbit_pool *p) {
     return t;
 }
 
-// Shared body of the single-list and batched calls (a pool with list ranges).
-static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
-                             const int64_t *d_offsets, int single_root, int64_t single_n, int M, int K,
-                             int32_t *d_new_roots, int32_t *host_root, const pbit_tune *tune, void *ws,
-                             size_t ws_bytes, cudaStream_t s) {
-    (void)K;
+// Enqueue a sort of a pool with list ranges (d_offsets) or of one list.
+static pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
+                                const int64_t *d_offsets, int single_root, int64_t single_n, int M,
+                                int32_t *d_new_roots, const pbit_tune *tune, void *ws, size_t ws_bytes,
+                                cudaStream_t s, Ctx *out) {
     Tune t;
     if (!resolve_tune(tune, pool->pool_size, pool->key_type, &t))
         return PBIT_EINVAL;
@@ -266,10 +322,12 @@ static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int
     Sizes z = compute_sizes(pool->pool_size, num_lists, pool->key_type, t, sms);
     Ctx c;
     std::vector<Memset> ms;
-    size_t need = bind(z, (unsigned char *)ws, &c, &ms);
+    const size_t need = bind(z, (unsigned char *)ws, &c, &ms);
     if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255))
         return ws_bytes < need ? PBIT_ENOMEM : PBIT_EINVAL;
     c.flags = pool->flags;
+    c.shared_pool = 1;
+    c.desc_next_stride = pool->next_stride_bytes;
     if (d_new_roots)
         c.new_roots = d_new_roots;
     ListDesc tmpl = pool_template(pool);
@@ -285,8 +343,12 @@ static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int
         d.out_base = 0;
         rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, &g_last_launches);
     }
-    if (rc != PBIT_OK)
-        return rc;
+    *out = c;
+    return rc;
+}
+
+// Read back the status (and the single root), synchronizing the stream.
+static pbit_status finish_call(const Ctx &c, int32_t *host_root, cudaStream_t s) {
     static thread_local int32_t *hbuf = nullptr;
     if (!hbuf && cudaMallocHost((void **)&hbuf, 64) != cudaSuccess)
         return PBIT_ECUDA;
@@ -294,17 +356,60 @@ static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int
         return PBIT_ECUDA;
     if (host_root && cudaMemcpyAsync(hbuf + 1, c.new_roots, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return PBIT_ECUDA;
+    if (g_prof.on && cudaMemcpyAsync(&g_prof.ctr, c.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PBIT_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return PBIT_ECUDA;
-    pbit_status st = map_status(hbuf[0]);
+    if (g_prof.on) {
+        g_prof.have_ctr = true;
+        g_prof.n = g_prof.ctr.n_virt;
+    }
+    const pbit_status st = map_status(hbuf[0]);
     if (st == PBIT_OK && host_root)
         *host_root = hbuf[1];
     return st;
 }
 
+static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
+                             const int64_t *d_offsets, int single_root, int64_t single_n, int M,
+                             int32_t *d_new_roots, int32_t *host_root, const pbit_tune *tune, void *ws,
+                             size_t ws_bytes, cudaStream_t s) {
+    Ctx c;
+    const pbit_status rc = enqueue_pool(pool, num_lists, d_roots, d_offsets, single_root, single_n, M,
+                                        d_new_roots, tune, ws, ws_bytes, s, &c);
+    if (rc != PBIT_OK)
+        return rc;
+    return finish_call(c, host_root, s);
+}
+
+// Byte ranges of a pool: the next[] region, and the key[] / prev[] regions
+// when they do not lie inside it (AoS keeps the key inside the node).
+struct PoolSpan {
+    size_t next_bytes, key_bytes, prev_bytes;
+    bool key_inside;
+    ptrdiff_t key_off;
+};
+
+static PoolSpan pool_span(const pbit_pool *p) {
+    PoolSpan r{};
+    const int64_t n = p->pool_size;
+    r.next_bytes = (size_t)(n > 0 ? (n - 1) * p->next_stride_bytes + 4 : 0);
+    const unsigned char *nb = (const unsigned char *)p->next, *kb = (const unsigned char *)p->key;
+    r.key_off = kb - nb;
+    r.key_inside = r.key_off >= 0 && r.key_off + (n > 0 ? (n - 1) * p->key_stride_bytes + p->key_type : 0) <=
+                                         (ptrdiff_t)r.next_bytes + p->next_stride_bytes;
+    if (r.key_inside)
+        r.next_bytes = (size_t)(n > 0 ? n * p->next_stride_bytes : 0);
+    r.key_bytes = r.key_inside ? 0 : (size_t)(n > 0 ? (n - 1) * p->key_stride_bytes + p->key_type : 0);
+    r.prev_bytes = (p->flags & PBIT_DOUBLY) ? (size_t)(n > 0 ? (n - 1) * p->prev_stride_bytes + 4 : 0) : 0;
+    return r;
+}
+
 }  // namespace pbit
 
 using namespace pbit;
+
+
 
 extern "C" {
 
@@ -351,7 +456,7 @@ pbit_status pbit_sort_list(const pbit_pool *pool, int32_t root, int64_t n, int32
     }
     if (root < 0 || root >= n)
         return PBIT_EBADLIST;
-    return sort_pool(pool, 1, nullptr, nullptr, root, n, M, K, nullptr, new_root_host, tune, ws, ws_bytes,
+    return sort_pool(pool, 1, nullptr, nullptr, root, n, M, nullptr, new_root_host, tune, ws, ws_bytes,
                      (cudaStream_t)stream);
 }
 
@@ -360,10 +465,129 @@ pbit_status pbit_sort_lists_batched(const pbit_pool *pool, int32_t num_lists, co
                                     const pbit_tune *tune, void *ws, size_t ws_bytes, void *stream) {
     if (!check_pool(pool, M, K) || num_lists < 1 || !d_roots || !d_offsets || !d_new_roots)
         return PBIT_EINVAL;
-    return sort_pool(pool, num_lists, d_roots, d_offsets, 0, 0, M, K, d_new_roots, nullptr, tune, ws, ws_bytes,
+    return sort_pool(pool, num_lists, d_roots, d_offsets, 0, 0, M, d_new_roots, nullptr, tune, ws, ws_bytes,
                      (cudaStream_t)stream);
 }
 
 int64_t pbit_last_launch_count(void) { return g_last_launches; }
+
+void pbit_profile_enable(int32_t on) { g_prof.on = on != 0; }
+
+int32_t pbit_profile_read(pbit_kernel_stat *out, int32_t max) {
+    if (!g_prof.on || !g_prof.start || !out || max <= 0)
+        return 0;
+    int32_t cnt = 0;
+    cudaEvent_t prev = g_prof.start;
+    for (auto &m : g_prof.marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, prev, m.second) != cudaSuccess)
+            return -1;
+        prev = m.second;
+        int32_t i = 0;
+        while (i < cnt && std::strncmp(out[i].name, m.first, sizeof(out[i].name)) != 0)
+            ++i;
+        if (i == cnt) {
+            if (cnt == max)
+                continue;
+            std::memset(&out[i], 0, sizeof(out[i]));
+            std::strncpy(out[i].name, m.first, sizeof(out[i].name) - 1);
+            ++cnt;
+        }
+        out[i].launches += 1;
+        out[i].ms += ms;
+    }
+    if (g_prof.have_ctr) {
+        const Counters &k = g_prof.ctr;
+        const double n = (double)g_prof.n, kb = (double)g_prof.kb;
+        for (int32_t i = 0; i < cnt; ++i) {
+            const char *nm = out[i].name;
+            double b = 0;
+            if (!std::strcmp(nm, "walk") || !std::strcmp(nm, "emit")) {
+                b = n * 2.0 * (4.0 + kb);
+            } else if (!std::strcmp(nm, "wyllie")) {
+                b = (double)g_prof.rcap * (16.0 + 24.0 * (double)g_prof.rounds);
+            } else if (!std::strcmp(nm, "seg_stats")) {
+                for (int it = 0; it < kMaxIters; ++it)
+                    b += (double)k.stat_elems[it] * kb;
+            } else if (!std::strcmp(nm, "pass")) {
+                for (int it = 0; it < kMaxIters; ++it)
+                    b += (double)k.pass_elems[it] * 2.0 * (4.0 + kb) - (double)k.pass_final_elems[it] * kb;
+            } else if (!std::strcmp(nm, "finish")) {
+                b = (double)k.fin_sort_elems * (kb + 8.0) + (double)k.fin_copy_elems * 8.0;
+            } else if (!std::strcmp(nm, "relink")) {
+                b = n * (g_prof.blocked_relink ? 24.0 : 8.0);
+            }
+            out[i].bytes = b;
+        }
+    }
+    return cnt;
+}
+
+pbit_status pbit_workspace_size_host(const pbit_pool *host_pool, const pbit_tune *tune, size_t *bytes) {
+    if (!host_pool || !bytes)
+        return PBIT_EINVAL;
+    size_t w = 0;
+    const pbit_status st = pbit_workspace_size(host_pool->pool_size, 1, host_pool->key_type, tune, &w);
+    if (st != PBIT_OK)
+        return st;
+    const PoolSpan sp = pool_span(host_pool);
+    *bytes = w + ((sp.next_bytes + 255) & ~(size_t)255) + ((sp.key_bytes + 255) & ~(size_t)255) +
+             ((sp.prev_bytes + 255) & ~(size_t)255) + 256;
+    return PBIT_OK;
+}
+
+pbit_status pbit_sort_list_host(const pbit_pool *host_pool, int32_t root, int64_t n, int32_t M, int32_t K,
+                                int32_t *new_root_host, const pbit_tune *tune, void *ws, size_t ws_bytes,
+                                void *stream) {
+    if (!check_pool(host_pool, M, K) || !new_root_host || n != host_pool->pool_size)
+        return PBIT_EINVAL;
+    if (n == 0) {
+        if (root != -1)
+            return PBIT_EBADLIST;
+        *new_root_host = -1;
+        return PBIT_OK;
+    }
+    if (root < 0 || root >= n)
+        return PBIT_EBADLIST;
+    size_t need = 0;
+    if (pbit_workspace_size_host(host_pool, tune, &need) != PBIT_OK)
+        return PBIT_EINVAL;
+    if (!ws || ws_bytes < need)
+        return PBIT_ENOMEM;
+    const PoolSpan sp = pool_span(host_pool);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned char *w = (unsigned char *)ws;
+    unsigned char *dnext = w;
+    w += (sp.next_bytes + 255) & ~(size_t)255;
+    unsigned char *dkey = w;
+    w += (sp.key_bytes + 255) & ~(size_t)255;
+    unsigned char *dprev = w;
+    w += (sp.prev_bytes + 255) & ~(size_t)255;
+    pbit_pool dp = *host_pool;
+    dp.next = (int32_t *)dnext;
+    dp.key = sp.key_inside ? (const void *)(dnext + sp.key_off) : (const void *)dkey;
+    if (host_pool->flags & PBIT_DOUBLY)
+        dp.prev = (int32_t *)dprev;
+    if (cudaMemcpyAsync(dnext, host_pool->next, sp.next_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return PBIT_ECUDA;
+    if (sp.key_bytes &&
+        cudaMemcpyAsync(dkey, host_pool->key, sp.key_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return PBIT_ECUDA;
+    if (sp.prev_bytes &&
+        cudaMemcpyAsync(dprev, host_pool->prev, sp.prev_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return PBIT_ECUDA;
+    Ctx c;
+    const size_t rest = ws_bytes - (size_t)(w - (unsigned char *)ws);
+    pbit_status rc = enqueue_pool(&dp, 1, nullptr, nullptr, root, n, M, nullptr, tune, w, rest, s, &c);
+    if (rc != PBIT_OK)
+        return rc;
+    // copy back unconditionally: on an error the device copy was not written
+    if (cudaMemcpyAsync(host_pool->next, dnext, sp.next_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PBIT_ECUDA;
+    if (sp.prev_bytes &&
+        cudaMemcpyAsync(host_pool->prev, dprev, sp.prev_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PBIT_ECUDA;
+    return finish_call(c, new_root_host, s);
+}
 
 }  // extern "C"

@@ -18,8 +18,8 @@
 
 namespace pbit {
 
-constexpr int kFTPB = 256;
-constexpr int kFItems = 16;
+constexpr int kFTPB = 512;
+constexpr int kFItems = 8;
 constexpr int kFCap = kFTPB * kFItems;  // largest bucket the finish kernel sorts
 constexpr int kFD = 4;
 constexpr int kFBins = 1 << kFD;
@@ -30,7 +30,7 @@ constexpr int finish_smem() {
 }
 
 template <typename KeyT>
-__global__ void __launch_bounds__(kFTPB) k_finish(Ctx c) {
+__global__ void __launch_bounds__(kFTPB, 2) k_finish(Ctx c) {
     extern __shared__ __align__(16) unsigned char f_smem[];
     KeyT *s_key = reinterpret_cast<KeyT *>(f_smem);
     int32_t *s_idx = reinterpret_cast<int32_t *>(f_smem + kFCap * sizeof(KeyT));
@@ -60,10 +60,14 @@ __global__ void __launch_bounds__(kFTPB) k_finish(Ctx c) {
         const int32_t *src_idx = c.idxb[buf] + start;
         int32_t *dst = c.F + start;
         if (mode == 0 || len <= 1) {
+            if (tid == 0)
+                atomicAdd((unsigned long long *)&c.ctr->fin_copy_elems, (unsigned long long)len);
             for (int j = tid; j < len; j += kFTPB)
                 dst[j] = src_idx[j];
             continue;
         }
+        if (tid == 0)
+            atomicAdd((unsigned long long *)&c.ctr->fin_sort_elems, (unsigned long long)len);
         if (len > kFCap) {
             set_status(c.status, kStOverflow);
             continue;
@@ -171,7 +175,9 @@ __global__ void __launch_bounds__(kFTPB) k_finish(Ctx c) {
     }
 }
 
-// Stage (d): relink.  One thread per sorted position.
+// Stage (d): relink, direct form: one thread per sorted position writes
+// next[s[q]] = s[q+1] straight into the pool (scattered 4-byte stores).  Used
+// when the lists live in different pools (the request server).
 __global__ void k_relink(Ctx c) {
     if (*(volatile int32_t *)c.status)
         return;
@@ -208,6 +214,95 @@ __global__ void k_relink(Ctx c) {
     }
 }
 
+// Stage (d), blocked form for lists sharing one pool.  Scattered 4-byte
+// stores into a pool much larger than L2 each cost a read-modify-write of a
+// DRAM granule; instead the (node, successor) pairs are first bucketed by
+// the node's pool block (2^rb nodes, a window of a few MB), then applied
+// block after block, so the stores of one window merge in L2 and leave as
+// full lines.  The two order buffers idxb[0], idxb[1] (free by now) hold the
+// pairs; bucket b owns slots [b << rb, (b << rb) + count).
+constexpr int kRelTPB = 256;
+constexpr int kRelItems = 16;
+constexpr int kRelTile = kRelTPB * kRelItems;
+constexpr int kMaxRelBuckets = 512;
+
+__global__ void __launch_bounds__(kRelTPB) k_relink_part(Ctx c, int rb) {
+    __shared__ int32_t s_cnt[kMaxRelBuckets];
+    __shared__ int32_t s_base[kMaxRelBuckets];
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int32_t nv = c.ctr->n_virt;
+    const int L = c.num_lists;
+    const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
+    const bool doubly = (c.flags & PBIT_DOUBLY) != 0;
+    int32_t *tv = c.idxb[0], *ts = c.idxb[1];
+    for (int64_t q0 = (int64_t)blockIdx.x * kRelTile; q0 < nv; q0 += (int64_t)gridDim.x * kRelTile) {
+        for (int b = threadIdx.x; b < nb; b += kRelTPB)
+            s_cnt[b] = 0;
+        __syncthreads();
+        int32_t vv[kRelItems], ss[kRelItems], rk[kRelItems];
+#pragma unroll
+        for (int i = 0; i < kRelItems; ++i) {
+            const int64_t q = q0 + i * kRelTPB + threadIdx.x;
+            vv[i] = -1;
+            if (q < nv) {
+                const int lst = upper_index(c.out_base, L, (int32_t)q);
+                const ListDesc &d = c.desc[lst];
+                const int32_t loc = c.F[q] - d.out_base;
+                const int64_t end = (int64_t)d.out_base + d.n;
+                int32_t succ = -1;
+                bool bad = loc < 0 || loc >= d.n;
+                if (q + 1 < end) {
+                    const int32_t ls = c.F[q + 1] - d.out_base;
+                    bad |= ls < 0 || ls >= d.n;
+                    succ = d.id_base + ls;
+                    if (doubly && !bad)
+                        *(int32_t *)((unsigned char *)d.prev + (int64_t)succ * d.prev_stride) = d.id_base + loc;
+                }
+                if (bad) {
+                    set_status(c.status, kStOverflow);
+                } else {
+                    vv[i] = d.id_base + loc;
+                    ss[i] = succ;
+                    if (q == d.out_base) {
+                        c.new_roots[lst] = vv[i];
+                        if (doubly)
+                            *(int32_t *)((unsigned char *)d.prev + (int64_t)vv[i] * d.prev_stride) = -1;
+                    }
+                    rk[i] = atomicAdd(&s_cnt[vv[i] >> rb], 1);
+                }
+            }
+        }
+        __syncthreads();
+        for (int b = threadIdx.x; b < nb; b += kRelTPB)
+            s_base[b] = s_cnt[b] ? atomicAdd(&c.rel_cursor[b], s_cnt[b]) : 0;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kRelItems; ++i) {
+            if (vv[i] >= 0) {
+                const int b = vv[i] >> rb;
+                const int64_t slot = ((int64_t)b << rb) + s_base[b] + rk[i];
+                tv[slot] = vv[i];
+                ts[slot] = ss[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_relink_apply(Ctx c, int rb) {
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int32_t *tv = c.idxb[0], *ts = c.idxb[1];
+    unsigned char *next = reinterpret_cast<unsigned char *>(c.desc[0].next);
+    const int64_t stride = c.desc[0].next_stride;
+    const int64_t mask = (1ll << rb) - 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.ncap; i += (int64_t)gridDim.x * blockDim.x) {
+        if ((i & mask) < c.rel_cursor[i >> rb])
+            *(int32_t *)(next + (int64_t)tv[i] * stride) = ts[i];
+    }
+}
+
 __global__ void k_empty_roots(Ctx c) {
     if (*(volatile int32_t *)c.status)
         return;
@@ -230,7 +325,8 @@ template <typename KeyT>
 static void launch_finish_t(const Ctx &c, cudaStream_t s, int sms) {
     constexpr int smem = finish_smem<KeyT>();
     cudaFuncSetAttribute(k_finish<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_finish<KeyT><<<(unsigned)(sms * 4), kFTPB, smem, s>>>(c);
+    k_finish<KeyT><<<(unsigned)(sms * 2), kFTPB, smem, s>>>(c);
+    prof_mark("finish", s);
 }
 
 void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
@@ -240,13 +336,37 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
     case 4: launch_finish_t<uint32_t>(c, s, sms); break;
     default: launch_finish_t<unsigned long long>(c, s, sms); break;
     }
-    const int64_t blocks = min((int64_t)sms * 16, max((int64_t)1, (c.ncap + 255) / 256));
-    k_relink<<<(unsigned)blocks, 256, 0, s>>>(c);
+    if (relink_blocked(c)) {
+        const int rb = relink_bucket_bits(c);
+        const int64_t pblocks = min((int64_t)sms * 8, max((int64_t)1, (c.ncap + kRelTile - 1) / kRelTile));
+        k_relink_part<<<(unsigned)pblocks, kRelTPB, 0, s>>>(c, rb);
+        const int64_t ablocks = min((int64_t)sms * 8, max((int64_t)1, (c.ncap + 255) / 256));
+        k_relink_apply<<<(unsigned)ablocks, 256, 0, s>>>(c, rb);
+    } else {
+        const int64_t blocks = min((int64_t)sms * 16, max((int64_t)1, (c.ncap + 255) / 256));
+        k_relink<<<(unsigned)blocks, 256, 0, s>>>(c);
+    }
+    prof_mark("relink", s);
     k_empty_roots<<<max(1, min(sms, (c.num_lists + 255) / 256)), 256, 0, s>>>(c);
+    prof_mark("relink", s);
 }
 
-void launch_check_done(const Ctx &c, int iters, cudaStream_t s) { k_check_done<<<1, 32, 0, s>>>(c, iters); }
+void launch_check_done(const Ctx &c, int iters, cudaStream_t s) {
+    k_check_done<<<1, 32, 0, s>>>(c, iters);
+    prof_mark("plan", s);
+}
 
 int finish_capacity() { return kFCap; }
+
+// Blocked relink when every list shares one pool (not the request server's
+// per-request pools): window of 2^rb nodes = at most 16 MB of next[].
+bool relink_blocked(const Ctx &c) { return c.shared_pool != 0; }
+int relink_bucket_bits(const Ctx &c) {
+    int rb = c.desc_next_stride <= 4 ? 22 : (c.desc_next_stride <= 8 ? 21 : 20);
+    while (rb < 31 && ((c.ncap + (1ll << rb) - 1) >> rb) > kMaxRelBuckets)
+        ++rb;
+    return rb;
+}
+int relink_max_buckets() { return kMaxRelBuckets; }
 
 }  // namespace pbit

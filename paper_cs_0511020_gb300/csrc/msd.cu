@@ -6,29 +6,30 @@
 // ascending (Sec. "Differences between sorting in descending and ascending
 // order").  Here every recursion level is one data-parallel pass over all
 // live buckets ("segments") at once: a stable counting split of each segment
-// into 2^D sub-segments laid out in ascending digit order, which is the same
-// order the ascending concatenation produces.
+// into 2^D sub-segments laid out in ascending digit order, which is the order
+// the ascending concatenation produces.
 //
-//   seg_stats     per pending segment: 16-bin histograms of every D-bit
-//                 window and the AND/OR of its keys (which bits still vary)
-//   plan_pending  pending segment -> active (window holding its top varying
-//                 bit), small (finished in shared memory) or done
-//   pass          per active segment tile: warp-ballot ranking, decoupled
-//                 look-back over the segment's tiles, stable scatter through
-//                 shared memory; fused: next-window histogram and AND/OR of
-//                 every output bucket
-//   plan          output buckets -> next active / pending / small / done
+// One iteration (= one recursion level for every live segment):
+//   seg_stats     pending segments: 16-bin histogram of the window under
+//                 their top bit and the AND/OR of their keys
+//   plan_pending  pending -> active / small / done / pending again (when the
+//                 top window does not vary, the segment retries one window
+//                 lower, at its highest varying bit)
+//   pass          per active tile: warp-ballot ranking, decoupled look-back
+//                 over the tiles of its segment, stable scatter through shared
+//                 memory; fused: next-window histogram and AND/OR per bucket
+//   plan_count / plan_scan / plan_write
+//                 output buckets -> next active / pending / small / done
 #include "pbit_internal.cuh"
 
 namespace pbit {
 
-constexpr int kTPB = 256;       // threads per pass / stats CTA
-constexpr int kItems = 16;      // items per thread in a pass tile
-constexpr int kTile = kTPB * kItems;  // 4096 elements per pass tile
-constexpr int kStatTile = 8192; // elements per seg_stats tile
-constexpr int kD = 4;           // GPU digit width (16 buckets, as the paper's K = 4)
+constexpr int kTPB = 256;             // threads per pass / stats CTA
+constexpr int kItems = 8;             // items per thread in a pass tile
+constexpr int kTile = kTPB * kItems;  // 2048 elements per pass tile
+constexpr int kStatTile = 8192;       // elements per seg_stats tile
+constexpr int kD = 4;                 // GPU digit width (16 buckets, as the paper's K = 4)
 constexpr int kBins = 1 << kD;
-constexpr int kMaxWin = 16;     // 64-bit keys / 4-bit windows
 static_assert(kTPB == kBins * kBins, "the next-window histogram flush maps one thread per counter");
 
 __host__ __device__ constexpr int tiles_of(int64_t len, int64_t tile) { return (int)((len + tile - 1) / tile); }
@@ -73,6 +74,15 @@ __device__ __forceinline__ unsigned long long low_mask(int bits) {
     return bits >= 64 ? ~0ull : ((1ull << bits) - 1ull);
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // ------------------------------------------------------------- plan_init
 // Lists become the first segments: empty lists vanish, lists up to the
 // cutoff go straight to the shared-memory finish, the rest are pending.
@@ -112,7 +122,7 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
         if (is_pend) {
             int k = s_pend_base + pp;
             if (k < c.seg_cap) {
-                c.pend[0][k] = Seg{start, n, 0, c.M};
+                c.pend[0][k] = Seg{start, n, 0, (int16_t)c.M, 0};
                 c.pend_tile_base[0][k] = s_tile_base + pt;
             } else {
                 set_status(c.status, kStOverflow);
@@ -128,7 +138,7 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
     }
     if (threadIdx.x == 0) {
         c.ctr->fin_count = s_fin_base;
-        c.ctr->pend_count[0] = min((int64_t)s_pend_base, c.seg_cap);
+        c.ctr->pend_count[0] = (int32_t)min((int64_t)s_pend_base, c.seg_cap);
         if (s_pend_base < c.seg_cap)
             c.pend_tile_base[0][s_pend_base] = s_tile_base;
         c.ctr->stat_tiles[0] = s_tile_base;
@@ -137,9 +147,12 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
 }
 
 // ------------------------------------------------------------- seg_stats
+// Histogram of the window [max(hi-D,0), hi) and AND/OR of every pending
+// segment, 8 keys per thread in flight.
 template <typename KeyT>
 __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
-    __shared__ uint32_t s_cnt[kMaxWin * kBins];
+    constexpr int kU = 8;
+    __shared__ uint32_t s_cnt[kBins];
     __shared__ unsigned long long s_and, s_or;
     __shared__ int s_tile;
     if (*(volatile int32_t *)c.status)
@@ -147,11 +160,9 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
     const int cur = it & 1;
     const int P = c.ctr->pend_count[cur];
     const int ntiles = c.ctr->stat_tiles[cur];
-    const KeyT *keys = reinterpret_cast<const KeyT *>(c.keyb[cur]);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned lt = lanemask_lt();
-    for (int i = threadIdx.x; i < kMaxWin * kBins; i += kTPB)
-        s_cnt[i] = 0;
+    if (threadIdx.x < kBins)
+        s_cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         s_and = ~0ull;
         s_or = 0ull;
@@ -169,62 +180,55 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         const int k = g - c.pend_tile_base[cur][s];
         const int64_t b0 = (int64_t)sg.start + (int64_t)k * kStatTile;
         const int cnt = (int)min((int64_t)kStatTile, (int64_t)sg.start + sg.len - b0);
-        const int hi = sg.hi;
-        const int nwin = (hi + kD - 1) / kD;
-        uint32_t wc[kMaxWin];
-#pragma unroll
-        for (int w = 0; w < kMaxWin; ++w)
-            wc[w] = 0;
+        const KeyT *keys = reinterpret_cast<const KeyT *>(c.keyb[sg.buf & 1]);
+        const int hi = sg.hi, lo = max(hi - kD, 0);
+        const unsigned dmask = (1u << (hi - lo)) - 1u;
+        if (threadIdx.x == 0)
+            atomicAdd((unsigned long long *)&c.ctr->stat_elems[it], (unsigned long long)cnt);
+        uint32_t wc = 0;
         unsigned long long a_and = ~0ull, a_or = 0ull;
-        for (int base = wid * 32; base < cnt; base += kTPB) {
-            const int pos = base + lane;
-            const bool valid = pos < cnt;
-            unsigned long long key = valid ? (unsigned long long)keys[b0 + pos] : 0ull;
-            if (valid) {
-                a_and &= key;
-                a_or |= key;
+        for (int base = wid * 32 * kU; base < cnt; base += kTPB * kU) {
+            unsigned long long kv[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int pos = base + u * 32 + lane;
+                kv[u] = pos < cnt ? (unsigned long long)keys[b0 + pos] : 0ull;
             }
-            const unsigned vm = __ballot_sync(kFull, valid);
 #pragma unroll
-            for (int w = 0; w < kMaxWin; ++w) {
-                if (w < nwin) {
-                    const int whi = hi - kD * w;
-                    const int wlo = max(whi - kD, 0);
-                    const unsigned dig = (unsigned)((key >> wlo) & ((1ull << (whi - wlo)) - 1));
-                    unsigned m = vm;
-#pragma unroll
-                    for (int b = 0; b < kD; ++b) {
-                        const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
-                        m &= ((lane >> b) & 1) ? bb : ~bb;
-                    }
-                    wc[w] += __popc(m);
+            for (int u = 0; u < kU; ++u) {
+                const int pos = base + u * 32 + lane;
+                const bool valid = pos < cnt;
+                if (valid) {
+                    a_and &= kv[u];
+                    a_or |= kv[u];
                 }
+                const unsigned dig = (unsigned)(kv[u] >> lo) & dmask;
+                unsigned m = __ballot_sync(kFull, valid);
+#pragma unroll
+                for (int b = 0; b < kD; ++b) {
+                    const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
+                    m &= ((lane >> b) & 1) ? bb : ~bb;
+                }
+                wc += __popc(m);
             }
         }
-        (void)lt;
-        // warp AND/OR
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a_and &= __shfl_xor_sync(kFull, a_and, o);
             a_or |= __shfl_xor_sync(kFull, a_or, o);
         }
-        if (lane < kBins) {
-#pragma unroll
-            for (int w = 0; w < kMaxWin; ++w)
-                if (w < nwin && wc[w])
-                    atomicAdd(&s_cnt[w * kBins + lane], wc[w]);
-        }
+        if (lane < kBins && wc)
+            atomicAdd(&s_cnt[lane], wc);
         if (lane == 0) {
             atomicAnd(&s_and, a_and);
             atomicOr(&s_or, a_or);
         }
         __syncthreads();
-        uint32_t *gh = c.phist[cur] + (int64_t)s * (kMaxWin * kBins);
-        for (int i = threadIdx.x; i < nwin * kBins; i += kTPB) {
-            uint32_t v = s_cnt[i];
+        if (threadIdx.x < kBins) {
+            const uint32_t v = s_cnt[threadIdx.x];
             if (v) {
-                atomicAdd(&gh[i], v);
-                s_cnt[i] = 0;
+                atomicAdd(&c.phist[cur][(int64_t)s * kBins + threadIdx.x], v);
+                s_cnt[threadIdx.x] = 0;
             }
         }
         if (threadIdx.x == 0) {
@@ -239,87 +243,109 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
 // ---------------------------------------------------------- plan_pending
 __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
     __shared__ int sh[40];
-    __shared__ int s_act_base, s_fin_base, s_tile_base;
+    __shared__ int s_act_base, s_re_base, s_re_tiles, s_tile_base;
     if (*(volatile int32_t *)c.status)
         return;
-    const int cur = it & 1;
+    const int cur = it & 1, nxt = cur ^ 1;
     const int P = c.ctr->pend_count[cur];
     if (threadIdx.x == 0) {
         s_act_base = c.ctr->act_count[cur];
-        s_fin_base = 0;
+        s_re_base = 0;
+        s_re_tiles = 0;
         s_tile_base = 0;
     }
     __syncthreads();
     int fin_total = 0;
     for (int r0 = 0; r0 < P; r0 += blockDim.x) {
         const int s = r0 + threadIdx.x;
-        int kind = 0;  // 1 fin copy, 2 fin sort, 3 active
-        Seg sg{0, 0, 0, 0};
-        int t = 0, w = 0;
+        int kind = 0;  // 1 fin copy, 2 fin sort, 3 active, 4 pending again
+        Seg sg{0, 0, 0, 0, 0};
+        int t = 0;
         if (s < P) {
             sg = c.pend[cur][s];
-            unsigned long long v = (c.por[cur][s] ^ c.pand[cur][s]) & low_mask(sg.hi);
+            const unsigned long long v = (c.por[cur][s] ^ c.pand[cur][s]) & low_mask(sg.hi);
             if (sg.len <= 1 || v == 0) {
                 kind = 1;
             } else {
                 t = top_bit(v);
                 if (sg.len <= c.cutoff)
                     kind = 2;
-                else {
-                    kind = 3;
-                    w = (sg.hi - 1 - t) / kD;
-                }
+                else
+                    kind = (t >= sg.hi - kD) ? 3 : 4;
             }
         }
-        int tf, ta;
-        int pf = block_excl_scan(kind == 1 || kind == 2, &tf, sh);
-        int pa = block_excl_scan(kind == 3, &ta, sh);
+        const int tiles = kind == 4 ? tiles_of(sg.len, kStatTile) : 0;
+        int tf, ta, tr, tt;
+        const int pf = block_excl_scan(kind == 1 || kind == 2, &tf, sh);
+        const int pa = block_excl_scan(kind == 3, &ta, sh);
+        const int pr = block_excl_scan(kind == 4, &tr, sh);
+        const int pt = block_excl_scan(tiles, &tt, sh);
         if (kind == 1 || kind == 2) {
-            int64_t k = (int64_t)c.ctr->fin_count + fin_total + pf;
+            const int64_t k = (int64_t)c.ctr->fin_count + fin_total + pf;
             if (k < c.fin_cap)
-                c.fin[k] = Fin{sg.start, sg.len, kind == 2 ? t + 1 : 0, ((kind == 2 ? 1 : 0) << 8) | cur};
+                c.fin[k] = Fin{sg.start, sg.len, kind == 2 ? t + 1 : 0, ((kind == 2 ? 1 : 0) << 8) | (sg.buf & 1)};
             else
                 set_status(c.status, kStOverflow);
-        }
-        if (kind == 3) {
-            int64_t a = (int64_t)s_act_base + pa;
+        } else if (kind == 3) {
+            const int64_t a = (int64_t)s_act_base + pa;
             if (a < c.seg_cap) {
-                const int hi2 = sg.hi - kD * w;
-                const int lo2 = max(hi2 - kD, 0);
-                c.act[cur][a] = Seg{sg.start, sg.len, lo2, hi2};
-                const uint32_t *src = c.phist[cur] + (int64_t)s * (kMaxWin * kBins) + w * kBins;
+                c.act[cur][a] = Seg{sg.start, sg.len, (int16_t)max(sg.hi - kD, 0), sg.hi, sg.buf};
+                const uint32_t *src = c.phist[cur] + (int64_t)s * kBins;
                 uint32_t *dst = c.act_hist[cur] + a * kBins;
                 for (int b = 0; b < kBins; ++b)
                     dst[b] = src[b];
             } else {
                 set_status(c.status, kStOverflow);
             }
+        } else if (kind == 4) {
+            const int64_t r = (int64_t)s_re_base + pr;
+            if (r < c.seg_cap) {
+                c.pend[nxt][r] = Seg{sg.start, sg.len, 0, (int16_t)(t + 1), sg.buf};
+                c.pend_tile_base[nxt][r] = s_re_tiles + pt;
+            } else {
+                set_status(c.status, kStOverflow);
+            }
         }
-        if (s < P) {  // leave the stats rows clean for their next use
-            uint32_t *row = c.phist[cur] + (int64_t)s * (kMaxWin * kBins);
-            for (int b = 0; b < kMaxWin * kBins; ++b)
-                row[b] = 0;
+        if (s < P) {  // leave the stats row clean for its next use
+            uint4 *row = reinterpret_cast<uint4 *>(c.phist[cur] + (int64_t)s * kBins);
+            row[0] = make_uint4(0, 0, 0, 0);
+            row[1] = make_uint4(0, 0, 0, 0);
+            row[2] = make_uint4(0, 0, 0, 0);
+            row[3] = make_uint4(0, 0, 0, 0);
             c.pand[cur][s] = ~0ull;
             c.por[cur][s] = 0ull;
         }
         fin_total += tf;
         __syncthreads();
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             s_act_base += ta;
+            s_re_base += tr;
+            s_re_tiles += tt;
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         c.ctr->fin_count += fin_total;
         c.ctr->act_count[cur] = (int32_t)min((int64_t)s_act_base, c.seg_cap);
+        c.ctr->pend_count[nxt] = (int32_t)min((int64_t)s_re_base, c.seg_cap);
+        c.ctr->stat_tiles[nxt] = s_re_tiles;
     }
     __syncthreads();
     // tile bases of all active segments of this pass
-    const int A = min((int64_t)s_act_base, c.seg_cap);
+    const int A = (int)min((int64_t)s_act_base, c.seg_cap);
+    long long my_elems = 0, my_final = 0;
     for (int r0 = 0; r0 < A; r0 += blockDim.x) {
         const int a = r0 + threadIdx.x;
-        int tiles = (a < A) ? tiles_of(c.act[cur][a].len, kTile) : 0;
+        int tiles = 0;
+        if (a < A) {
+            const Seg sa = c.act[cur][a];
+            tiles = tiles_of(sa.len, kTile);
+            my_elems += sa.len;
+            if (sa.lo == 0)
+                my_final += sa.len;
+        }
         int tt;
-        int pt = block_excl_scan(tiles, &tt, sh);
+        const int pt = block_excl_scan(tiles, &tt, sh);
         if (a < A)
             c.act_tile_base[cur][a] = s_tile_base + pt;
         __syncthreads();
@@ -327,12 +353,15 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
             s_tile_base += tt;
         __syncthreads();
     }
+    if (my_elems) {
+        atomicAdd((unsigned long long *)&c.ctr->pass_elems[it], (unsigned long long)my_elems);
+        atomicAdd((unsigned long long *)&c.ctr->pass_final_elems[it], (unsigned long long)my_final);
+    }
     if (threadIdx.x == 0) {
-        if (A < c.seg_cap + 1)
-            c.act_tile_base[cur][A] = s_tile_base;
+        c.act_tile_base[cur][A] = s_tile_base;
         if (s_tile_base > c.tile_cap)
             set_status(c.status, kStOverflow);
-        c.ctr->num_tiles[cur] = min((int64_t)s_tile_base, c.tile_cap);
+        c.ctr->num_tiles[cur] = (int32_t)min((int64_t)s_tile_base, c.tile_cap);
     }
 }
 
@@ -343,11 +372,9 @@ struct PassSmem {
     uint32_t tile_cnt[kBins];
     int32_t gbase[kBins];
     uint32_t nh[kBins * kBins];
-    int32_t st_seg[2], st_start[2], st_cnt[2], st_k[2], st_tile[2];
-    int32_t st_shk[2], st_shi[2];
-    int32_t nt[2];   // next tile id, one slot per stage
+    int32_t g, seg, cnt, k, shk, shi;
     int32_t err;
-    alignas(8) uint64_t bar[2];
+    alignas(8) uint64_t bar;
 };
 
 template <typename KeyT>
@@ -356,41 +383,87 @@ struct PassLayout {
     static constexpr int kIdxBytes = kTile * 4 + 32;
     static constexpr int kStage = ((kKeyBytes + kIdxBytes + 127) / 128) * 128;
     static constexpr int kHdr = ((int)sizeof(PassSmem) + 127) / 128 * 128;
-    static constexpr int kTotal = kHdr + 2 * kStage;
+    static constexpr int kTotal = kHdr + kStage;
+    static constexpr int kMinBlocks = sizeof(KeyT) == 8 ? 3 : 4;
 };
 
-// Issue the bulk copies of tile g into stage st (one thread).
+// Issue the bulk copies of tile g into the stage buffer (one thread).
 template <typename KeyT>
-__device__ __forceinline__ void pass_issue(const Ctx &c, int cur, int g, int st, PassSmem &S,
-                                           unsigned char *stage, int A) {
+__device__ __forceinline__ void pass_issue(const Ctx &c, int cur, int g, PassSmem &S, unsigned char *stage,
+                                           int A) {
     const int s = upper_index(c.act_tile_base[cur], A, g);
     const Seg sg = c.act[cur][s];
     const int k = g - c.act_tile_base[cur][s];
     const int64_t start = (int64_t)sg.start + (int64_t)k * kTile;
     const int cnt = (int)min((int64_t)kTile, (int64_t)sg.start + sg.len - start);
     constexpr int W = (int)sizeof(KeyT);
-    const unsigned char *kb = c.keyb[cur];
-    const unsigned char *ib = reinterpret_cast<const unsigned char *>(c.idxb[cur]);
+    const unsigned char *kb = c.keyb[sg.buf & 1];
+    const unsigned char *ib = reinterpret_cast<const unsigned char *>(c.idxb[sg.buf & 1]);
     const int64_t k_lo = (start * W) & ~15ll, k_hi = ((start + cnt) * W + 15) & ~15ll;
     const int64_t i_lo = (start * 4) & ~15ll, i_hi = ((start + cnt) * 4 + 15) & ~15ll;
-    S.st_seg[st] = s;
-    S.st_start[st] = (int32_t)start;
-    S.st_cnt[st] = cnt;
-    S.st_k[st] = k;
-    S.st_tile[st] = g;
-    S.st_shk[st] = (int32_t)((start * W - k_lo) / W);
-    S.st_shi[st] = (int32_t)((start * 4 - i_lo) / 4);
+    S.seg = s;
+    S.cnt = cnt;
+    S.k = k;
+    S.shk = (int32_t)((start * W - k_lo) / W);
+    S.shi = (int32_t)((start * 4 - i_lo) / 4);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&S.bar[st], (uint32_t)((k_hi - k_lo) + (i_hi - i_lo)));
-    bulk_g2s(stage, kb + k_lo, (uint32_t)(k_hi - k_lo), &S.bar[st]);
-    bulk_g2s(stage + PassLayout<KeyT>::kKeyBytes, ib + i_lo, (uint32_t)(i_hi - i_lo), &S.bar[st]);
+    mbar_arrive_expect_tx(&S.bar, (uint32_t)((k_hi - k_lo) + (i_hi - i_lo)));
+    bulk_g2s(stage, kb + k_lo, (uint32_t)(k_hi - k_lo), &S.bar);
+    bulk_g2s(stage + PassLayout<KeyT>::kKeyBytes, ib + i_lo, (uint32_t)(i_hi - i_lo), &S.bar);
 }
 
+// Warp 0: walk back over the earlier tiles of the segment until every digit
+// has met an inclusive prefix (this tile's own aggregate was published
+// already).  The warp stays converged (one 128-byte read of 16 words per
+// step); a word is (epoch, state, count) in one 64-bit store, so relaxed
+// accesses suffice.
+__device__ __forceinline__ uint32_t lookback(const Ctx &c, int g0, uint32_t tot, uint32_t epoch, int lane,
+                                             int *err) {
+    const int d = lane & (kBins - 1);
+    const bool owner = lane < kBins;
+    uint32_t excl = 0;
+    bool done = !owner;
+    int gp = g0 - 1;
+    uint64_t t0 = 0;
+    long long spins = 0;
+    while (true) {
+        unsigned long long x = 0;
+        bool ready = true;
+        if (!done) {
+            x = ld_relaxed_u64(c.lb + (int64_t)gp * kBins + d);
+            ready = ((uint32_t)(x >> 56) == (epoch & 0xff)) && (((x >> 54) & 3ull) != 0);
+        }
+        if (!__all_sync(kFull, ready)) {
+            if (++spins == 1)
+                t0 = globaltimer_ns();
+            if ((spins & 15) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
+                *err = 1;
+                break;
+            }
+            continue;
+        }
+        spins = 0;
+        if (!done) {
+            excl += (uint32_t)(x & ((1ull << 54) - 1));
+            done = ((x >> 54) & 3ull) == kLbIncl;
+        }
+        if (__all_sync(kFull, done))
+            break;
+        --gp;
+    }
+    if (owner)
+        st_relaxed_u64(c.lb + (int64_t)g0 * kBins + d, lb_pack(epoch, kLbIncl, (unsigned long long)excl + tot));
+    return excl;
+}
+
+// One CTA works on one tile at a time (tile ids taken in order from a
+// counter, so every earlier tile of the segment is already being processed);
+// several CTAs per SM overlap each other's loads, look-backs and stores.
 template <typename KeyT>
-__global__ void __launch_bounds__(kTPB, 2) k_pass(Ctx c, int it) {
+__global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx c, int it) {
     extern __shared__ __align__(128) unsigned char smem[];
     PassSmem &S = *reinterpret_cast<PassSmem *>(smem);
-    unsigned char *stages = smem + PassLayout<KeyT>::kHdr;
+    unsigned char *stage = smem + PassLayout<KeyT>::kHdr;
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1, nxt = cur ^ 1;
@@ -417,56 +490,40 @@ __global__ void __launch_bounds__(kTPB, 2) k_pass(Ctx c, int it) {
         return;
 
     if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
+        mbar_init(&S.bar, 1);
         fence_mbar_init();
-    }
-    for (int i = tid; i < kBins * kBins; i += kTPB)
-        S.nh[i] = 0;
-    __syncthreads();
-
-    KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[nxt]);
-    int32_t *oidx = c.idxb[nxt];
-    uint32_t phase[2] = {0, 0};
-    int st = 0;
-    if (tid == 0) {
         S.err = 0;
-        int g = atomicAdd(&c.ctr->tile_ctr[it], 1);
-        S.nt[0] = g;
-        if (g < ntiles)
-            pass_issue<KeyT>(c, cur, g, 0, S, stages, A);
     }
+    S.nh[tid] = 0;
     __syncthreads();
-    int g = S.nt[0];
-    while (g < ntiles) {
-        unsigned char *stage = stages + st * PassLayout<KeyT>::kStage;
-        // prefetch the next tile into the other stage
+    uint32_t phase = 0;
+    while (true) {
         if (tid == 0) {
-            int g2 = atomicAdd(&c.ctr->tile_ctr[it], 1);
-            S.nt[st ^ 1] = g2;
-            if (g2 < ntiles)
-                pass_issue<KeyT>(c, cur, g2, st ^ 1, S, stages + (st ^ 1) * PassLayout<KeyT>::kStage, A);
+            const int g = atomicAdd(&c.ctr->tile_ctr[it], 1);
+            S.g = g;
+            if (g < ntiles)
+                pass_issue<KeyT>(c, cur, g, S, stage, A);
         }
-        const bool landed = mbar_wait_bounded(&S.bar[st], phase[st], 1ll << 26);
+        __syncthreads();
+        const int g = S.g;
+        if (g >= ntiles)
+            break;
+        const bool landed = mbar_wait_bounded(&S.bar, phase, 1ll << 26);
         if (!__syncthreads_and(landed)) {
             set_status(c.status, PBIT_ETIMEOUT);
-            // wait (bounded) for the copies still in flight before leaving
-            if (tid == 0) {
-                mbar_wait_bounded(&S.bar[st], phase[st], 1ll << 26);
-                if (S.nt[st ^ 1] < ntiles)
-                    mbar_wait_bounded(&S.bar[st ^ 1], phase[st ^ 1], 1ll << 26);
-            }
+            if (tid == 0)  // wait (bounded) for the copy still in flight before leaving
+                mbar_wait_bounded(&S.bar, phase, 1ll << 26);
             return;
         }
-        phase[st] ^= 1;
-        const int s = S.st_seg[st];
-        const int k = S.st_k[st];
-        const int cnt = S.st_cnt[st];
+        phase ^= 1;
+        const int s = S.seg;
+        const int k = S.k;
+        const int cnt = S.cnt;
         const Seg sg = c.act[cur][s];
         const int lo = sg.lo, hi = sg.hi;
         const unsigned dmask = (1u << (hi - lo)) - 1u;
-        const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + S.st_shk[st];
-        const int32_t *si = reinterpret_cast<const int32_t *>(stage + PassLayout<KeyT>::kKeyBytes) + S.st_shi[st];
+        const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + S.shk;
+        const int32_t *si = reinterpret_cast<const int32_t *>(stage + PassLayout<KeyT>::kKeyBytes) + S.shi;
 
         // ---- load + warp-ballot ranking (order: warp, item, lane == memory order)
         KeyT key[kItems];
@@ -488,83 +545,41 @@ __global__ void __launch_bounds__(kTPB, 2) k_pass(Ctx c, int it) {
                 peers &= ((dig >> b) & 1u) ? bb : ~bb;
                 mine &= ((lane >> b) & 1) ? bb : ~bb;
             }
-            const uint32_t before = __shfl_sync(kFull, run, (int)dig);
-            rnk[i] = before + __popc(peers & lt);
+            rnk[i] = __shfl_sync(kFull, run, (int)dig) + __popc(peers & lt);
             run += __popc(mine);
         }
         if (lane < kBins)
             S.wcnt[wid][lane] = run;
         __syncthreads();
-        // ---- tile histogram, warp prefixes, look-back (lanes 0..15 of warp 0)
-        if (wid == 0 && lane < kBins) {
-            const int d = lane;
-            uint32_t tot = 0;
+        // ---- tile histogram and prefixes; publish this tile's aggregate
+        uint32_t tot = 0;
+        if (wid == 0) {
+            const int d = lane & (kBins - 1);
+            if (lane < kBins) {
 #pragma unroll
-            for (int w = 0; w < kTPB / 32; ++w) {
-                uint32_t x = S.wcnt[w][d];
-                S.wcnt[w][d] = tot;
-                tot += x;
+                for (int w = 0; w < kTPB / 32; ++w) {
+                    const uint32_t x = S.wcnt[w][d];
+                    S.wcnt[w][d] = tot;
+                    tot += x;
+                }
+                S.tile_cnt[d] = tot;
             }
-            S.tile_cnt[d] = tot;
-            // exclusive scan over the 16 digits
-            uint32_t incl = tot;
+            uint32_t incl = (lane < kBins) ? tot : 0u;
 #pragma unroll
             for (int o = 1; o < kBins; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffu, incl, o);
-                if (d >= o)
+                const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
                     incl += y;
             }
-            S.tile_off[d] = incl - tot;
-            if (d == kBins - 1)
-                S.tile_off[kBins] = incl;
-            // decoupled look-back over earlier tiles of the same segment
-            const int g0 = S.st_tile[st];
-            unsigned long long *lbw = c.lb + (int64_t)g0 * kBins + d;
-            uint32_t excl = 0;
-            if (k == 0) {
-                st_release_u64(lbw, lb_pack(epoch, kLbIncl, tot));
-            } else {
-                st_release_u64(lbw, lb_pack(epoch, kLbAgg, tot));
-                int gp = g0 - 1;
-                long long spins = 0;
-                uint64_t t0 = 0;
-                while (true) {
-                    unsigned long long x = ld_acquire_u64(c.lb + (int64_t)gp * kBins + d);
-                    const uint32_t ep = (uint32_t)(x >> 56);
-                    const unsigned long long stt = (x >> 54) & 3ull;
-                    if (ep != (epoch & 0xff) || stt == 0) {
-                        ++spins;
-                        if (spins == 1)
-                            t0 = globaltimer_ns();
-                        if (spins > (1ll << 26) || ((spins & 63) == 0 && globaltimer_ns() - t0 > kWaitLimitNs)) {
-                            set_status(c.status, PBIT_ETIMEOUT);
-                            S.err = 1;
-                            break;
-                        }
-                        if (spins > 64)
-                            __nanosleep(64);
-                        continue;
-                    }
-                    excl += (uint32_t)(x & ((1ull << 54) - 1));
-                    if (stt == kLbIncl)
-                        break;
-                    --gp;
-                }
-                st_release_u64(lbw, lb_pack(epoch, kLbIncl, (unsigned long long)excl + tot));
+            if (lane < kBins) {
+                S.tile_off[d] = incl - tot;
+                if (d == kBins - 1)
+                    S.tile_off[kBins] = incl;
+                st_relaxed_u64(c.lb + (int64_t)g * kBins + d, lb_pack(epoch, k == 0 ? kLbIncl : kLbAgg, tot));
             }
-            uint32_t bex = 0;
-            const uint32_t *h = c.act_hist[cur] + (int64_t)s * kBins;
-            for (int b = 0; b < d; ++b)
-                bex += h[b];
-            S.gbase[d] = sg.start + (int32_t)bex + (int32_t)excl;
         }
         __syncthreads();
-        if (S.err) {  // a look-back gave up: write nothing, drain the prefetch
-            if (tid == 0 && S.nt[st ^ 1] < ntiles)
-                mbar_wait_bounded(&S.bar[st ^ 1], phase[st ^ 1], 1ll << 26);
-            return;
-        }
-        // ---- local scatter into the stage buffer (now free: all items are in registers)
+        // ---- local scatter into the stage buffer (free now: all items are in registers)
         KeyT *ok = reinterpret_cast<KeyT *>(stage);
         int32_t *oi = reinterpret_cast<int32_t *>(stage + PassLayout<KeyT>::kKeyBytes);
 #pragma unroll
@@ -577,27 +592,48 @@ __global__ void __launch_bounds__(kTPB, 2) k_pass(Ctx c, int it) {
                 oi[lp] = idx[i];
             }
         }
+        // ---- look-back (warp 0) overlaps the other warps' scatter
+        if (wid == 0) {
+            int err = 0;
+            const uint32_t excl = (k == 0) ? 0u : lookback(c, g, tot, epoch, lane, &err);
+            if (lane < kBins) {
+                const int d = lane;
+                uint32_t bex = 0;
+                const uint32_t *h = c.act_hist[cur] + (int64_t)s * kBins;
+                for (int b = 0; b < d; ++b)
+                    bex += h[b];
+                S.gbase[d] = sg.start + (int32_t)bex + (int32_t)excl;
+            }
+            if (err && lane == 0) {
+                set_status(c.status, PBIT_ETIMEOUT);
+                S.err = 1;
+            }
+        }
         __syncthreads();
+        if (S.err)  // a look-back gave up: write nothing
+            return;
         // ---- coalesced write-out (+ next-window histogram)
-        const int nlo = max(lo - kD, 0);
-        const unsigned nmask = (1u << (lo - nlo)) - 1u;
+        const int seg_end = sg.start + sg.len;
+        KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(sg.buf & 1) ^ 1]);
+        int32_t *oidx = c.idxb[(sg.buf & 1) ^ 1];
         if (lo == 0) {
             for (int j = tid; j < cnt; j += kTPB) {
-                const KeyT kk = ok[j];
-                const unsigned dig = (unsigned)((unsigned long long)kk >> lo) & dmask;
+                const unsigned dig = (unsigned)((unsigned long long)ok[j] >> lo) & dmask;
                 const int dst = S.gbase[dig] + (j - (int)S.tile_off[dig]);
-                if (dst < sg.start || dst >= sg.start + sg.len) {
+                if (dst < sg.start || dst >= seg_end) {
                     set_status(c.status, kStOverflow);
                     continue;
                 }
                 c.F[dst] = oi[j];
             }
         } else {
+            const int nlo = max(lo - kD, 0);
+            const unsigned nmask = (1u << (lo - nlo)) - 1u;
             for (int j = tid; j < cnt; j += kTPB) {
                 const KeyT kk = ok[j];
                 const unsigned dig = (unsigned)((unsigned long long)kk >> lo) & dmask;
                 const int dst = S.gbase[dig] + (j - (int)S.tile_off[dig]);
-                if (dst < sg.start || dst >= sg.start + sg.len) {
+                if (dst < sg.start || dst >= seg_end) {
                     set_status(c.status, kStOverflow);
                     continue;
                 }
@@ -629,24 +665,20 @@ __global__ void __launch_bounds__(kTPB, 2) k_pass(Ctx c, int it) {
                 }
             }
             __syncthreads();
-            {
-                const uint32_t v = S.nh[tid];
-                if (v) {
-                    atomicAdd(&c.nh[cur][(int64_t)s * kBins * kBins + tid], v);
-                    S.nh[tid] = 0;
-                }
+            const uint32_t v = S.nh[tid];
+            if (v) {
+                atomicAdd(&c.nh[cur][(int64_t)s * kBins * kBins + tid], v);
+                S.nh[tid] = 0;
             }
         }
         __syncthreads();
-        g = S.nt[st ^ 1];
-        st ^= 1;
     }
 }
 
 // ------------------------------------------------------------------ plan
+// kinds: 0 none, 1 fin copy, 2 fin sort, 3 next active, 4 pending
 __device__ __forceinline__ int classify_bucket(const Ctx &c, int cur, int s, const Seg &sg, int d,
                                                uint32_t cnt, int *t_out) {
-    // 0 none, 1 fin copy, 2 fin sort, 3 next active, 4 pending
     if (cnt == 0 || sg.lo == 0)
         return 0;
     const int64_t r = (int64_t)s * kBins + d;
@@ -660,128 +692,154 @@ __device__ __forceinline__ int classify_bucket(const Ctx &c, int cur, int s, con
     return (t + kD >= sg.lo) ? 3 : 4;
 }
 
-__global__ void __launch_bounds__(1024) k_plan(Ctx c, int it) {
+// per active segment: how many next-active, pending, small/done buckets and
+// stats tiles its buckets produce
+__global__ void k_plan_count(Ctx c, int it) {
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1;
+    const int A = c.ctr->act_count[cur];
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A; s += gridDim.x * blockDim.x) {
+        const Seg sg = c.act[cur][s];
+        int na = 0, np = 0, nf = 0, nt = 0;
+        const uint32_t *h = c.act_hist[cur] + (int64_t)s * kBins;
+        for (int d = 0; d < kBins; ++d) {
+            int t = 0;
+            const uint32_t cnt = h[d];
+            const int kd = classify_bucket(c, cur, s, sg, d, cnt, &t);
+            na += kd == 3;
+            np += kd == 4;
+            nf += (kd == 1 || kd == 2);
+            nt += (kd == 4) ? tiles_of(cnt, kStatTile) : 0;
+        }
+        c.plan_cnt[s] = make_int4(na, np, nf, nt);
+    }
+}
+
+// exclusive scan of the per-segment counts (one CTA), new counters
+__global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
     __shared__ int sh[40];
-    __shared__ int s_act, s_pend, s_fin, s_tiles;
+    __shared__ int s_a, s_p, s_f, s_t;
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1, nxt = cur ^ 1;
     const int A = c.ctr->act_count[cur];
     if (threadIdx.x == 0) {
-        s_act = 0;
-        s_pend = 0;
-        s_fin = c.ctr->fin_count;
-        s_tiles = 0;
+        s_a = 0;
+        s_p = c.ctr->pend_count[nxt];  // after the segments plan_pending re-queued
+        s_f = c.ctr->fin_count;
+        s_t = c.ctr->stat_tiles[nxt];
     }
     __syncthreads();
     for (int r0 = 0; r0 < A; r0 += blockDim.x) {
         const int s = r0 + threadIdx.x;
-        Seg sg{0, 0, 0, 0};
-        uint32_t h[kBins];
-        int na = 0, np = 0, nf = 0, nt = 0;
-        if (s < A) {
-            sg = c.act[cur][s];
-            for (int d = 0; d < kBins; ++d)
-                h[d] = c.act_hist[cur][(int64_t)s * kBins + d];
-            for (int d = 0; d < kBins; ++d) {
-                int t = 0;
-                int kd = classify_bucket(c, cur, s, sg, d, h[d], &t);
-                na += kd == 3;
-                np += kd == 4;
-                nf += (kd == 1 || kd == 2);
-                nt += (kd == 4) ? tiles_of(h[d], kStatTile) : 0;
-            }
-        } else {
-            for (int d = 0; d < kBins; ++d)
-                h[d] = 0;
-        }
+        const int4 v = (s < A) ? c.plan_cnt[s] : make_int4(0, 0, 0, 0);
         int ta, tp, tf, tt;
-        int pa = block_excl_scan(na, &ta, sh);
-        int pp = block_excl_scan(np, &tp, sh);
-        int pf = block_excl_scan(nf, &tf, sh);
-        int pt = block_excl_scan(nt, &tt, sh);
-        if (s < A) {
-            int64_t a = (int64_t)s_act + pa, p = (int64_t)s_pend + pp, f = (int64_t)s_fin + pf;
-            int64_t tb = (int64_t)s_tiles + pt;
-            int32_t bstart = sg.start;
-            for (int d = 0; d < kBins; ++d) {
-                int t = 0;
-                const uint32_t cnt = h[d];
-                const int kd = classify_bucket(c, cur, s, sg, d, cnt, &t);
-                if (kd == 1 || kd == 2) {
-                    if (f < c.fin_cap)
-                        c.fin[f] = Fin{bstart, (int32_t)cnt, kd == 2 ? t + 1 : 0, ((kd == 2 ? 1 : 0) << 8) | nxt};
-                    else
-                        set_status(c.status, kStOverflow);
-                    ++f;
-                } else if (kd == 3) {
-                    if (a < c.seg_cap) {
-                        const int nlo = max(sg.lo - kD, 0);
-                        c.act[nxt][a] = Seg{bstart, (int32_t)cnt, nlo, sg.lo};
-                        const uint32_t *src = c.nh[cur] + ((int64_t)s * kBins + d) * kBins;
-                        uint32_t *dst = c.act_hist[nxt] + a * kBins;
-                        for (int b = 0; b < kBins; ++b)
-                            dst[b] = src[b];
-                    } else {
-                        set_status(c.status, kStOverflow);
-                    }
-                    ++a;
-                } else if (kd == 4) {
-                    if (p < c.seg_cap) {
-                        c.pend[nxt][p] = Seg{bstart, (int32_t)cnt, 0, t + 1};
-                        c.pend_tile_base[nxt][p] = (int32_t)tb;
-                    } else {
-                        set_status(c.status, kStOverflow);
-                    }
-                    tb += tiles_of(cnt, kStatTile);
-                    ++p;
-                }
-                bstart += (int32_t)cnt;
-            }
-        }
+        const int pa = block_excl_scan(v.x, &ta, sh);
+        const int pp = block_excl_scan(v.y, &tp, sh);
+        const int pf = block_excl_scan(v.z, &tf, sh);
+        const int pt = block_excl_scan(v.w, &tt, sh);
+        if (s < A)
+            c.plan_cnt[s] = make_int4(s_a + pa, s_p + pp, s_f + pf, s_t + pt);
         __syncthreads();
         if (threadIdx.x == 0) {
-            s_act += ta;
-            s_pend += tp;
-            s_fin += tf;
-            s_tiles += tt;
+            s_a += ta;
+            s_p += tp;
+            s_f += tf;
+            s_t += tt;
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        c.ctr->act_count[nxt] = (int32_t)min((int64_t)s_act, c.seg_cap);
-        c.ctr->pend_count[nxt] = (int32_t)min((int64_t)s_pend, c.seg_cap);
-        if (s_pend < c.seg_cap)
-            c.pend_tile_base[nxt][s_pend] = s_tiles;
-        c.ctr->stat_tiles[nxt] = s_tiles;
-        c.ctr->fin_count = (int32_t)min((int64_t)s_fin, c.fin_cap);
+        if (s_a > c.seg_cap || s_p > c.seg_cap || s_f > c.fin_cap)
+            set_status(c.status, kStOverflow);
+        c.ctr->act_count[nxt] = (int32_t)min((int64_t)s_a, c.seg_cap);
+        c.ctr->pend_count[nxt] = (int32_t)min((int64_t)s_p, c.seg_cap);
+        if (s_p <= c.seg_cap)
+            c.pend_tile_base[nxt][s_p] = s_t;
+        c.ctr->stat_tiles[nxt] = s_t;
+        c.ctr->fin_count = (int32_t)min((int64_t)s_f, c.fin_cap);
+    }
+}
+
+__global__ void k_plan_write(Ctx c, int it) {
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1, nxt = cur ^ 1;
+    const int A = c.ctr->act_count[cur];
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A; s += gridDim.x * blockDim.x) {
+        const Seg sg = c.act[cur][s];
+        const int4 o = c.plan_cnt[s];
+        int64_t a = o.x, p = o.y, f = o.z, tb = o.w;
+        const uint32_t *h = c.act_hist[cur] + (int64_t)s * kBins;
+        int32_t bstart = sg.start;
+        for (int d = 0; d < kBins; ++d) {
+            int t = 0;
+            const uint32_t cnt = h[d];
+            const int kd = classify_bucket(c, cur, s, sg, d, cnt, &t);
+            if (kd == 1 || kd == 2) {
+                if (f < c.fin_cap)
+                    c.fin[f] = Fin{bstart, (int32_t)cnt, kd == 2 ? t + 1 : 0,
+                                   ((kd == 2 ? 1 : 0) << 8) | ((sg.buf & 1) ^ 1)};
+                ++f;
+            } else if (kd == 3) {
+                if (a < c.seg_cap) {
+                    c.act[nxt][a] = Seg{bstart, (int32_t)cnt, (int16_t)max(sg.lo - kD, 0), sg.lo, (sg.buf & 1) ^ 1};
+                    const uint4 *src = reinterpret_cast<const uint4 *>(c.nh[cur] + ((int64_t)s * kBins + d) * kBins);
+                    uint4 *dst = reinterpret_cast<uint4 *>(c.act_hist[nxt] + a * kBins);
+                    dst[0] = src[0];
+                    dst[1] = src[1];
+                    dst[2] = src[2];
+                    dst[3] = src[3];
+                }
+                ++a;
+            } else if (kd == 4) {
+                if (p < c.seg_cap) {
+                    c.pend[nxt][p] = Seg{bstart, (int32_t)cnt, 0, (int16_t)(t + 1), (sg.buf & 1) ^ 1};
+                    c.pend_tile_base[nxt][p] = (int32_t)tb;
+                }
+                tb += tiles_of(cnt, kStatTile);
+                ++p;
+            }
+            bstart += (int32_t)cnt;
+        }
     }
 }
 
 // ------------------------------------------------------------- launchers
 template <typename KeyT>
-static void launch_pass_t(const Ctx &c, int it, cudaStream_t s, int sms) {
+static void launch_iter_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     const int smem = PassLayout<KeyT>::kTotal;
     cudaFuncSetAttribute(k_pass<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    const int per_sm = (2 * smem + 2048 <= 227 * 1024) ? 2 : 1;
+    const int per_sm = PassLayout<KeyT>::kMinBlocks;
+    const unsigned pblocks = (unsigned)max(1, min(sms * 4, (int)((c.seg_cap + 255) / 256)));
     k_seg_stats<KeyT><<<sms * 4, kTPB, 0, s>>>(c, it);
+    prof_mark("seg_stats", s);
     k_plan_pending<<<1, 1024, 0, s>>>(c, it);
+    prof_mark("plan", s);
     k_pass<KeyT><<<sms * per_sm, kTPB, smem, s>>>(c, it);
-    k_plan<<<1, 1024, 0, s>>>(c, it);
+    prof_mark("pass", s);
+    k_plan_count<<<pblocks, 256, 0, s>>>(c, it);
+    k_plan_scan<<<1, 1024, 0, s>>>(c, it);
+    k_plan_write<<<pblocks, 256, 0, s>>>(c, it);
+    prof_mark("plan", s);
 }
 
-void launch_plan_init(const Ctx &c, cudaStream_t s) { k_plan_init<<<1, 1024, 0, s>>>(c); }
+void launch_plan_init(const Ctx &c, cudaStream_t s) {
+    k_plan_init<<<1, 1024, 0, s>>>(c);
+    prof_mark("plan", s);
+}
 
 void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms) {
     switch (c.key_bytes) {
-    case 1: launch_pass_t<uint8_t>(c, it, s, sms); break;
-    case 2: launch_pass_t<uint16_t>(c, it, s, sms); break;
-    case 4: launch_pass_t<uint32_t>(c, it, s, sms); break;
-    default: launch_pass_t<unsigned long long>(c, it, s, sms); break;
+    case 1: launch_iter_t<uint8_t>(c, it, s, sms); break;
+    case 2: launch_iter_t<uint16_t>(c, it, s, sms); break;
+    case 4: launch_iter_t<uint32_t>(c, it, s, sms); break;
+    default: launch_iter_t<unsigned long long>(c, it, s, sms); break;
     }
 }
 
-int64_t launches_per_iteration() { return 4; }
+int64_t launches_per_iteration() { return 6; }
 int pass_tile() { return kTile; }
 int stat_tile() { return kStatTile; }
 int digit_bits() { return kD; }

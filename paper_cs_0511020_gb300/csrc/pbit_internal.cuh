@@ -33,11 +33,13 @@ struct ListDesc {
 
 // A contiguous run of the order buffers that still has to be sorted on the
 // key bits [0, hi); an active segment is split in the next pass on [lo, hi).
+// buf = which of the two order buffers currently holds it.
 struct Seg {
     int32_t start;
     int32_t len;
-    int32_t lo;
-    int32_t hi;
+    int16_t lo;
+    int16_t hi;
+    int32_t buf;
 };
 
 // A finished-or-small run: mode 0 = copy the node ids to the final buffer,
@@ -61,6 +63,14 @@ struct Counters {
     int32_t pend_count[2];
     int32_t num_tiles[2];
     int32_t stat_tiles[2];
+    int32_t task_next;         // work counter of the ranking walk
+    int32_t pad0;
+    // element counts for the per-kernel algorithmic-byte accounting
+    long long pass_elems[kMaxIters];
+    long long pass_final_elems[kMaxIters];
+    long long stat_elems[kMaxIters];
+    long long fin_sort_elems;
+    long long fin_copy_elems;
     int32_t tile_ctr[kMaxIters];
     int32_t stat_ctr[kMaxIters];
     int32_t pad[16];
@@ -77,6 +87,8 @@ struct Ctx {
     int32_t cutoff;     // buckets <= cutoff are finished in shared memory
     int32_t flags;      // PBIT_SIGNED | PBIT_DESCENDING | PBIT_FLOAT | PBIT_DOUBLY
     int32_t CH;         // ranking chunk entries
+    int32_t shared_pool;       // all lists in one pool (blocked relink possible)
+    int64_t desc_next_stride;  // next[] stride of that pool
     int64_t ncap;       // capacity of the order buffers (pool size)
     int32_t R0;         // hash-ruler tasks
     int32_t Rcap;       // R0 + num_lists
@@ -96,7 +108,8 @@ struct Ctx {
     int64_t *wy[2];     // packed (succ << 32) | suffix length, ping-pong
     int32_t *chunk_task;
     int32_t *chunk_j0;
-    int32_t *chunk_data;
+    int32_t *chunk_data;        // chunk_cap x CH node ids (virtual positions)
+    unsigned char *chunk_key;   // chunk_cap x CH sort keys
     unsigned char *keyb[2];
     int32_t *idxb[2];
     int32_t *F;
@@ -108,11 +121,13 @@ struct Ctx {
     unsigned long long *bor[2];
     Seg *pend[2];
     int32_t *pend_tile_base[2];
-    uint32_t *phist[2];         // seg_cap x 16 windows x 16 bins
+    uint32_t *phist[2];         // seg_cap x 16 bins (window under hi)
     unsigned long long *pand[2];
     unsigned long long *por[2];
+    int4 *plan_cnt;             // seg_cap per-segment counts -> offsets
     Fin *fin;
     unsigned long long *lb;     // tile_cap x 16 look-back words
+    int32_t *rel_cursor;        // blocked relink: pairs per node block
     int32_t *new_roots;
 };
 
@@ -269,6 +284,10 @@ struct Launch {
     int sms;
 };
 
+// Per-kernel event markers (profiling mode of engine.cu; no-ops otherwise):
+// call after every launch with the kernel's name.
+void prof_mark(const char *name, cudaStream_t s);
+
 // kernel entry points (defined in rank.cu / msd.cu / finish.cu)
 void launch_setup(const Ctx &c, const int64_t *d_offsets, const int32_t *d_roots, int mode,
                   const ListDesc *host_desc_tmpl, cudaStream_t s, int sms);
@@ -281,6 +300,9 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms);
 void launch_check_done(const Ctx &c, int iters, cudaStream_t s);
 int64_t launches_per_iteration();
 int finish_capacity();
+bool relink_blocked(const Ctx &c);
+int relink_bucket_bits(const Ctx &c);
+int relink_max_buckets();
 int pass_tile();
 int stat_tile();
 int digit_bits();

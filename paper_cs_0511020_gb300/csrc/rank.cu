@@ -6,11 +6,11 @@
 //
 //   setup     list descriptors, hash rulers, the root task of every list
 //   walk      every ruler walks next[] to the next ruler, writing the nodes it
-//             visits into chunks (one dependent gather per hop)
+//             visits and their sort keys into chunks (one dependent gather of
+//             next[] and one independent gather of key[] per hop)
 //   wyllie    pointer jumping over the ruler sublists -> offset of each sublist
 //   validate  the root's ruler chain must end at NULL after exactly n nodes
-//   emit      chunks -> (ord_idx, ord_key) at their ranks, keys gathered and
-//             mapped to unsigned sort keys
+//   emit      chunks -> (ord_idx, ord_key) at their ranks
 #include "pbit_internal.cuh"
 
 namespace pbit {
@@ -104,45 +104,92 @@ __global__ void __launch_bounds__(1024) k_setup(Ctx c, ListDesc t, const int64_t
 }
 
 // ------------------------------------------------------------------- walk
-// Warps own a static block of tasks; idle lanes refill from it, so a long
-// sub-walk keeps one lane busy instead of a whole block.  Chunks of CH node
-// ids are taken from a per-warp super-chunk of kSuper chunks, so the global
-// bump allocator sees one atomic per kSuper chunks.
+// Every task (a ruler) walks next[] until the next ruler or NULL, one hop per
+// loop trip per lane; the key of each visited node is gathered in the same
+// trip (an independent load beside the dependent next[] load) and stored,
+// already mapped to its sort key, next to the node id.  Warps take 64 tasks
+// at a time from a global counter and hand them to idle lanes, so a long
+// sub-walk occupies one lane, not a warp or a block.  Chunks of CH entries
+// come from a per-warp super-chunk of kSuper chunks.
 constexpr int kSuper = 64;
+constexpr int kTaskBatch = 64;
 
-__global__ void __launch_bounds__(256) k_walk(Ctx c) {
+// Chunk entries are staged per lane in shared memory and written 8 at a time
+// (a full 32-byte sector of node ids), so no partially written sector is
+// left in L2 to be read back from DRAM when it is evicted.
+constexpr int kStageN = 8;
+constexpr int kStagePad = kStageN + 1;  // odd row stride: conflict-free
+
+template <typename KeyT>
+__device__ __forceinline__ void flush_group(const Ctx &c, KeyT *ckey, int64_t base, const int32_t *si,
+                                            const KeyT *sk, int cnt) {
+    int32_t *di = c.chunk_data + base;
+    KeyT *dk = ckey + base;
+    if (cnt == kStageN) {
+        reinterpret_cast<int4 *>(di)[0] = make_int4(si[0], si[1], si[2], si[3]);
+        reinterpret_cast<int4 *>(di)[1] = make_int4(si[4], si[5], si[6], si[7]);
+        if constexpr (sizeof(KeyT) == 4) {
+            reinterpret_cast<uint4 *>(dk)[0] = make_uint4(sk[0], sk[1], sk[2], sk[3]);
+            reinterpret_cast<uint4 *>(dk)[1] = make_uint4(sk[4], sk[5], sk[6], sk[7]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < kStageN; ++i)
+                dk[i] = sk[i];
+        }
+    } else {
+        for (int i = 0; i < cnt; ++i) {
+            di[i] = si[i];
+            dk[i] = sk[i];
+        }
+    }
+}
+
+template <typename KeyT>
+__global__ void __launch_bounds__(256, 6) k_walk(Ctx c) {
+    __shared__ int32_t s_i[256 * kStagePad];
+    __shared__ KeyT s_k[256 * kStagePad];
     if (*(volatile int32_t *)c.status)
         return;
     const int lane = threadIdx.x & 31;
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int32_t *my_i = s_i + threadIdx.x * kStagePad;
+    KeyT *my_k = s_k + threadIdx.x * kStagePad;
     const int32_t ntask = c.Rcap;
-    const int32_t per = (int32_t)((ntask + nwarps - 1) / nwarps);
-    const int32_t t_begin = (int32_t)min((int64_t)ntask, gwarp * per);
-    const int32_t t_end = (int32_t)min((int64_t)ntask, (int64_t)t_begin + per);
     const int32_t nv = c.ctr->n_virt;
     const int32_t log2S = c.log2S;
     const int32_t CH = c.CH;
     const unsigned lt = lanemask_lt();
+    KeyT *ckey = reinterpret_cast<KeyT *>(c.chunk_key);
 
-    int32_t next_t = t_begin;  // warp-uniform
-    int32_t pool_next = 0, pool_end = 0;  // warp-uniform
+    int32_t q_next = 0, q_end = 0;  // warp-uniform task queue
+    bool exhausted = false;         // warp-uniform
+    int32_t pool_next = 0, pool_end = 0;  // warp-uniform super-chunk
 
     int32_t t = -1, v = 0, j = 0, chunk = 0;
-    int32_t saved = -1, power = 1, lam = 0;  // Brent cycle detection
-    int32_t *nxt = nullptr;
-    int64_t nstride = 4;
+    int32_t saved = -1;  // Brent-style cycle check: the node seen at hop 2^k
+    const unsigned char *nxt = nullptr, *kp = nullptr;
+    int32_t nstride = 4, kstride = 4;
     int32_t dn = 0, did = 0, dob = 0;
+    bool aos = false;
 
     while (true) {
-        // ---- refill idle lanes with the warp's next tasks
-        bool idle = (t < 0);
-        unsigned im = __ballot_sync(kFull, idle);
-        if (im != 0 && next_t < t_end) {
-            int32_t cand = next_t + __popc(im & lt);
-            next_t += __popc(im);
-            if (idle && cand < t_end) {
-                // find the start node of task cand
+        const bool idle = (t < 0);
+        const unsigned im = __ballot_sync(kFull, idle);
+        if (im != 0 && q_next >= q_end && !exhausted) {
+            int32_t base = 0;
+            if (lane == 0)
+                base = atomicAdd(&c.ctr->task_next, kTaskBatch);
+            base = __shfl_sync(kFull, base, 0);
+            if (base >= ntask) {
+                exhausted = true;
+            } else {
+                q_next = base;
+                q_end = min(base + kTaskBatch, ntask);
+            }
+        }
+        if (im != 0 && q_next < q_end) {
+            const int32_t cand = q_next + __popc(im & lt);
+            q_next = min(q_end, q_next + __popc(im));
+            if (idle && cand < q_end) {
                 int32_t p = -1, lst = -1;
                 if (cand < c.R0) {
                     if (((int64_t)cand << log2S) < nv) {
@@ -150,7 +197,7 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c) {
                         lst = upper_index(c.out_base, c.num_lists, p);
                     }
                 } else {
-                    int32_t i = cand - c.R0;
+                    const int32_t i = cand - c.R0;
                     if (c.root_task[i] == cand) {
                         lst = i;
                         p = c.desc[i].out_base + c.desc[i].root;
@@ -159,29 +206,31 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c) {
                 if (p >= 0) {
                     const ListDesc &d = c.desc[lst];
                     t = cand;
-                    nxt = d.next;
-                    nstride = d.next_stride;
+                    nxt = reinterpret_cast<const unsigned char *>(d.next);
+                    kp = d.key;
+                    nstride = (int32_t)d.next_stride;
+                    kstride = (int32_t)d.key_stride;
                     dn = d.n;
                     did = d.id_base;
                     dob = d.out_base;
+                    aos = sizeof(KeyT) == 4 && nstride == 8 && kstride == 8 && kp == nxt + 4 &&
+                          (reinterpret_cast<uintptr_t>(nxt) & 7) == 0;
                     v = p - dob;
                     j = 0;
                     saved = -1;
-                    power = 1;
-                    lam = 0;
                     c.task_list[cand] = lst;
                 }
             }
         }
         bool active = (t >= 0);
         if (!__any_sync(kFull, active)) {
-            if (next_t >= t_end)
+            if (exhausted && q_next >= q_end)
                 break;
             continue;
         }
         // ---- chunk allocation for lanes starting a new chunk
-        bool need = active && (j % CH == 0);
-        unsigned nm = __ballot_sync(kFull, need);
+        const bool need = active && (j % CH == 0);
+        const unsigned nm = __ballot_sync(kFull, need);
         if (nm) {
             const int32_t cnt = __popc(nm);
             const int32_t avail = pool_end - pool_next;
@@ -212,20 +261,33 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c) {
             }
         }
         if (active) {
-            c.chunk_data[(int64_t)chunk * CH + (j % CH)] = dob + v;
+            const int64_t node = (int64_t)(did + v);
+            int32_t raw;
+            KeyT key;
+            if (aos) {
+                const uint2 nk = *reinterpret_cast<const uint2 *>(nxt + node * 8);
+                raw = (int32_t)nk.x;
+                key = (KeyT)nk.y;
+            } else {
+                raw = *reinterpret_cast<const int32_t *>(nxt + node * nstride);
+                key = load_key_raw<KeyT>(kp + node * kstride);
+            }
+            const int e = j % CH;
+            const int slot = e & (kStageN - 1);
+            my_i[slot] = dob + v;
+            my_k[slot] = sort_key<KeyT>(key, c.flags, c.M);
             ++j;
-            int32_t raw = *(const int32_t *)((const unsigned char *)nxt + (int64_t)(did + v) * nstride);
             bool done = false;
             int32_t succ = -1;
             if (raw == -1) {
                 done = true;
             } else {
-                int32_t w = raw - did;
+                const int32_t w = raw - did;
                 if (raw < did || w >= dn) {
                     set_status(c.status, PBIT_EBADLIST);
                     done = true;
                 } else {
-                    int32_t p = dob + w;
+                    const int32_t p = dob + w;
                     if (is_ruler(p, log2S, nv)) {
                         succ = p >> log2S;
                         done = true;
@@ -233,16 +295,14 @@ __global__ void __launch_bounds__(256) k_walk(Ctx c) {
                         set_status(c.status, PBIT_EBADLIST);  // cycle or longer than the list
                         done = true;
                     } else {
-                        if (lam == power) {
-                            saved = w;
-                            power <<= 1;
-                            lam = 0;
-                        }
-                        ++lam;
+                        if ((j & (j - 1)) == 0)
+                            saved = w;  // a cycle of length l is met again before j doubles past l
                         v = w;
                     }
                 }
             }
+            if (slot == kStageN - 1 || done)
+                flush_group<KeyT>(c, ckey, (int64_t)chunk * CH + (e - slot), my_i, my_k, slot + 1);
             if (done) {
                 c.task_len[t] = j;
                 c.task_succ[t] = succ;
@@ -299,6 +359,10 @@ __global__ void k_validate(Ctx c, int fin) {
     }
 }
 
+// Each warp moves 32 chunks: lane l first fetches the metadata of chunk l
+// (task, offset in the task, the task's list and rank) so the dependent
+// metadata loads of 32 chunks overlap; then the chunks are copied four at a
+// time with all loads issued before the stores.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_emit(Ctx c, int fin) {
     if (*(volatile int32_t *)c.status)
@@ -308,30 +372,55 @@ __global__ void __launch_bounds__(256) k_emit(Ctx c, int fin) {
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nchunks = min((int64_t)c.ctr->chunk_next, c.chunk_cap);
     const int64_t *w = c.wy[fin];
+    const KeyT *ckey = reinterpret_cast<const KeyT *>(c.chunk_key);
     KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[0]);
     int32_t *oidx = c.idxb[0];
     const int CH = c.CH;  // == 32
-    for (int64_t ch = gwarp; ch < nchunks; ch += nwarps) {
-        int32_t t = c.chunk_task[ch];
-        if (t < 0)
-            continue;
-        int32_t j0 = c.chunk_j0[ch];
-        int32_t len = c.task_len[t];
-        int32_t lst = c.task_list[t];
-        const ListDesc &d = c.desc[lst];
-        uint32_t suffix = (uint32_t)((uint64_t)w[t]);
-        int32_t cnt = min(CH, len - j0);
-        int64_t pos0 = (int64_t)d.out_base + ((int64_t)d.n - (int64_t)suffix) + j0;
-        if (lane < cnt) {
-            int32_t p = c.chunk_data[ch * CH + lane];
-            int64_t pos = pos0 + lane;
-            if (pos < d.out_base || pos >= (int64_t)d.out_base + d.n) {
-                set_status(c.status, PBIT_EBADLIST);
-            } else {
-                int32_t loc = p - d.out_base;
-                KeyT k = load_key_raw<KeyT>(d.key + (int64_t)(d.id_base + loc) * d.key_stride);
-                okey[pos] = sort_key<KeyT>(k, c.flags, c.M);
-                oidx[pos] = p;
+    for (int64_t ch0 = gwarp * 32; ch0 < nchunks; ch0 += nwarps * 32) {
+        // per-lane metadata of chunk ch0 + lane
+        int32_t m_pos = 0, m_cnt = 0;
+        const int64_t mc = ch0 + lane;
+        if (mc < nchunks) {
+            const int32_t t = c.chunk_task[mc];
+            if (t >= 0) {
+                const int32_t j0 = c.chunk_j0[mc];
+                const int32_t len = c.task_len[t];
+                const int32_t lst = c.task_list[t];
+                const uint32_t suffix = (uint32_t)((uint64_t)w[t]);
+                const int32_t n = c.desc[lst].n, ob = c.desc[lst].out_base;
+                m_cnt = min(CH, len - j0);
+                const int64_t pos0 = (int64_t)ob + ((int64_t)n - (int64_t)suffix) + j0;
+                if (pos0 < ob || pos0 + m_cnt > (int64_t)ob + n) {
+                    set_status(c.status, PBIT_EBADLIST);
+                    m_cnt = 0;
+                }
+                m_pos = (int32_t)pos0;
+            }
+        }
+        const int nc = (int)min((int64_t)32, nchunks - ch0);
+        for (int b = 0; b < nc; b += 4) {
+            int32_t vi[4];
+            KeyT vk[4];
+            int32_t pos[4];
+            bool ok[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int src = min(b + u, 31);
+                const int32_t cnt = __shfl_sync(kFull, m_cnt, src);
+                pos[u] = __shfl_sync(kFull, m_pos, src) + lane;
+                ok[u] = (b + u < nc) && lane < cnt;
+                if (ok[u]) {
+                    const int64_t e = (ch0 + b + u) * CH + lane;
+                    vi[u] = c.chunk_data[e];
+                    vk[u] = ckey[e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (ok[u]) {
+                    okey[pos[u]] = vk[u];
+                    oidx[pos[u]] = vi[u];
+                }
             }
         }
     }
@@ -345,23 +434,34 @@ void launch_setup(const Ctx &c, const int64_t *d_offsets, const int32_t *d_roots
     if (tmpl)
         t = *tmpl;
     k_setup<<<1, 1024, 0, s>>>(c, t, d_offsets, d_roots, mode);
+    prof_mark("setup", s);
 }
 
 void launch_walk(const Ctx &c, cudaStream_t s, int sms) {
-    int64_t warps_needed = (c.Rcap + 31) / 32;  // at least one task per lane
-    int64_t blocks = min((int64_t)sms * 8, max((int64_t)1, (warps_needed + 7) / 8));
-    k_walk<<<(unsigned)blocks, 256, 0, s>>>(c);
+    const int64_t warps_needed = (c.Rcap + 31) / 32;  // at least one task per lane
+    const unsigned blocks = (unsigned)min((int64_t)sms * 8, max((int64_t)1, (warps_needed + 7) / 8));
+    switch (c.key_bytes) {
+    case 1: k_walk<uint8_t><<<blocks, 256, 0, s>>>(c); break;
+    case 2: k_walk<uint16_t><<<blocks, 256, 0, s>>>(c); break;
+    case 4: k_walk<uint32_t><<<blocks, 256, 0, s>>>(c); break;
+    default: k_walk<unsigned long long><<<blocks, 256, 0, s>>>(c); break;
+    }
+    prof_mark("walk", s);
 }
 
 void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds) {
     int64_t blocks = min((int64_t)sms * 8, max((int64_t)1, ((int64_t)c.Rcap + 255) / 256));
     k_wy_init<<<(unsigned)blocks, 256, 0, s>>>(c);
-    for (int r = 0; r < rounds; ++r)
+    prof_mark("wyllie", s);
+    for (int r = 0; r < rounds; ++r) {
         k_wy_round<<<(unsigned)blocks, 256, 0, s>>>(c, r & 1);
+        prof_mark("wyllie", s);
+    }
 }
 
 void launch_validate_emit(const Ctx &c, int fin, cudaStream_t s, int sms) {
     k_validate<<<max(1, min(sms, (c.num_lists + 255) / 256)), 256, 0, s>>>(c, fin);
+    prof_mark("validate", s);
     unsigned blocks = (unsigned)(sms * 8);
     switch (c.key_bytes) {
     case 1: k_emit<uint8_t><<<blocks, 256, 0, s>>>(c, fin); break;
@@ -369,6 +469,7 @@ void launch_validate_emit(const Ctx &c, int fin, cudaStream_t s, int sms) {
     case 4: k_emit<uint32_t><<<blocks, 256, 0, s>>>(c, fin); break;
     default: k_emit<unsigned long long><<<blocks, 256, 0, s>>>(c, fin); break;
     }
+    prof_mark("emit", s);
 }
 
 }  // namespace pbit

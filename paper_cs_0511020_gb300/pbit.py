@@ -18,8 +18,9 @@ OK, EINVAL, ENOMEM, EBADLIST, ETIMEOUT, ECUDA, EAGAIN, EPENDING = range(8)
 SIGNED, DESCENDING, DOUBLY, FLOAT = 1, 2, 4, 8
 
 EXPORTS = ("pbit_status_string", "pbit_workspace_size", "pbit_sort_list", "pbit_sort_lists_batched",
-           "pbit_last_launch_count", "pbit_serve_create", "pbit_serve_submit", "pbit_serve_poll",
-           "pbit_serve_wait", "pbit_serve_stats", "pbit_serve_destroy")
+           "pbit_workspace_size_host", "pbit_sort_list_host", "pbit_last_launch_count",
+           "pbit_profile_enable", "pbit_profile_read", "pbit_serve_create", "pbit_serve_submit",
+           "pbit_serve_poll", "pbit_serve_wait", "pbit_serve_stats", "pbit_serve_destroy")
 
 
 class PbitError(RuntimeError):
@@ -34,6 +35,11 @@ class Pool(ctypes.Structure):
                 ("key_type", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("pool_size", ctypes.c_int64), ("prev", ctypes.c_void_p),
                 ("prev_stride_bytes", ctypes.c_int64)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
 
 
 class Tune(ctypes.Structure):
@@ -63,6 +69,15 @@ def lib():
                                               ctypes.c_size_t, vp]
         L.pbit_last_launch_count.restype = i64
         L.pbit_last_launch_count.argtypes = []
+        L.pbit_workspace_size_host.restype = ctypes.c_int
+        L.pbit_workspace_size_host.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.pbit_sort_list_host.restype = ctypes.c_int
+        L.pbit_sort_list_host.argtypes = [vp, i32, i64, i32, i32, ctypes.POINTER(i32), vp, vp,
+                                          ctypes.c_size_t, vp]
+        L.pbit_profile_enable.restype = None
+        L.pbit_profile_enable.argtypes = [i32]
+        L.pbit_profile_read.restype = i32
+        L.pbit_profile_read.argtypes = [vp, i32]
         _lib = L
     return _lib
 
@@ -173,3 +188,47 @@ def sort_lists_batched(next_t, key_t, roots_t, offsets_t, M=None, K=4, flags=0, 
 
 def last_launch_count() -> int:
     return int(lib().pbit_last_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Per-kernel CUDA-event timing of the following sort calls on this thread."""
+    lib().pbit_profile_enable(1 if on else 0)
+
+
+def profile_read() -> list:
+    """[{name, launches, ms, bytes}] for the last sort call on this thread."""
+    arr = (KernelStat * 32)()
+    n = lib().pbit_profile_read(ctypes.addressof(arr), 32)
+    if n < 0:
+        raise PbitError(ECUDA, "pbit_profile_read")
+    return [dict(name=arr[i].name.decode(), launches=arr[i].launches, ms=arr[i].ms, bytes=arr[i].bytes)
+            for i in range(n)]
+
+
+def host_pool(next_h, key_h, flags: int = 0) -> Pool:
+    """SoA pool over HOST tensors/arrays (torch CPU tensors, pinned or not)."""
+    kb = key_h.element_size()
+    return Pool(next_h.data_ptr(), 4, key_h.data_ptr(), kb, kb, flags, next_h.numel(), 0, 0)
+
+
+def workspace_size_host(pool: Pool, tune=None) -> int:
+    out = ctypes.c_size_t(0)
+    tune, tp = _tune_ptr(tune)
+    st = lib().pbit_workspace_size_host(ctypes.addressof(pool), tp, ctypes.byref(out))
+    if st != OK:
+        raise PbitError(st, "pbit_workspace_size_host")
+    return int(out.value)
+
+
+def sort_pool_list_host(pool: Pool, root: int, n: int, M: int, K: int = 4, ws=None, tune=None, stream=None,
+                        check: bool = True):
+    """pbit_sort_list_host: the pool is in host memory; returns (status, new_root)."""
+    if ws is None:
+        ws = alloc_workspace(workspace_size_host(pool, tune))
+    tune, tp = _tune_ptr(tune)
+    nr = ctypes.c_int32(-7)
+    st = lib().pbit_sort_list_host(ctypes.addressof(pool), int(root), int(n), int(M), int(K), ctypes.byref(nr),
+                                   tp, ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    if check and st != OK:
+        raise PbitError(st, "pbit_sort_list_host")
+    return st, int(nr.value)

@@ -238,3 +238,26 @@ def test_tune_variants(pb):
     for tune in ({"smem_cutoff": 1024}, {"ruler_stride": 8}, {"ruler_stride": 256},
                  {"smem_cutoff": 256, "ruler_stride": 64}):
         _check_vs_oracle(pb, nxt, key, root, 32, tune=tune)
+
+
+@pytest.mark.parametrize("pattern", ["low18", "mid_const", "hi_lo_only", "two_values", "u64_sparse"])
+def test_constant_windows(pb, pattern):
+    """Keys whose top or middle digit windows never vary: exercises the
+    skipping of constant windows (pending segments re-queued one window lower,
+    buckets whose next window is constant)."""
+    n = 300000
+    g = I.rng(161 + len(pattern))
+    nxt, root = I.random_list(n, 162)
+    if pattern == "low18":
+        key = g.integers(0, 1 << 18, n, dtype=np.uint32)
+    elif pattern == "mid_const":
+        key = (g.integers(0, 1 << 6, n, dtype=np.uint32) << np.uint32(26)) | np.uint32(0x5A5A << 8) | \
+            g.integers(0, 256, n, dtype=np.uint32)
+    elif pattern == "hi_lo_only":
+        key = (g.integers(0, 3, n, dtype=np.uint32) << np.uint32(30)) | g.integers(0, 16, n, dtype=np.uint32)
+    elif pattern == "two_values":
+        key = np.where(g.random(n) < 0.5, 0x10000, 0x10001).astype(np.uint32)
+    else:
+        key = (g.integers(0, 5, n, dtype=np.uint64) << np.uint64(50)) | \
+            (g.integers(0, 1 << 20, n, dtype=np.uint64) << np.uint64(3))
+    _check_vs_oracle(pb, nxt, key, root, 8 * key.itemsize)
