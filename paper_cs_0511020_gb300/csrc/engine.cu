@@ -185,25 +185,27 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms) 
     for (int b = 0; b < 2; ++b)
         x.idxb[b] = (int32_t *)take((size_t)z.ncap * 4 + 64);
     x.F = (int32_t *)take((size_t)z.ncap * 4 + 64);
+    x.row_cap = 2 * (z.ncap / pass_tile()) + 18 * z.seg_cap + 64;
+    x.scan_cap = z.ncap / ((int64_t)pass_tile() * scan_rows()) + z.seg_cap + 2;
     for (int b = 0; b < 2; ++b) {
         x.act[b] = (Seg *)take(sizeof(Seg) * (size_t)z.seg_cap);
         x.act_hist[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * bins);
         x.act_tile_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
-        x.nh[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * bins * bins);
-        zero(x.nh[b], 0, 4 * (size_t)z.seg_cap * bins * bins);
+        x.act_chunk_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
+        x.act_nrow_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
+        x.tcnt[b] = (uint32_t *)take(4 * (size_t)x.row_cap * bins);
         x.band[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap * bins);
         zero(x.band[b], 0xff, 8 * (size_t)z.seg_cap * bins);
         x.bor[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap * bins);
         zero(x.bor[b], 0, 8 * (size_t)z.seg_cap * bins);
         x.pend[b] = (Seg *)take(sizeof(Seg) * (size_t)z.seg_cap);
         x.pend_tile_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
-        x.phist[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * bins);
-        zero(x.phist[b], 0, 4 * (size_t)z.seg_cap * bins);
         x.pand[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap);
         zero(x.pand[b], 0xff, 8 * (size_t)z.seg_cap);
         x.por[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap);
         zero(x.por[b], 0, 8 * (size_t)z.seg_cap);
     }
+    x.ctot = (uint32_t *)take(4 * (size_t)x.scan_cap * bins);
     x.plan_cnt = (int4 *)take(sizeof(int4) * (size_t)z.seg_cap);
     x.fin = (Fin *)take(sizeof(Fin) * (size_t)z.fin_cap);
     x.lb = (unsigned long long *)take(8 * (size_t)z.tile_cap * bins);

@@ -76,6 +76,9 @@ __global__ void __launch_bounds__(kFTPB, 2) k_finish(Ctx c) {
         KeyT key[kFItems];
         int32_t idx[kFItems];
         unsigned long long a_and = ~0ull, a_or = 0ull;
+        // item rounds of this warp that hold data (warp-uniform)
+        const int wbase = wid * (32 * kFItems);
+        const int nit = len <= wbase ? 0 : min(kFItems, (len - wbase + 31) / 32);
 #pragma unroll
         for (int i = 0; i < kFItems; ++i) {
             const int pos = wid * (32 * kFItems) + i * 32 + lane;
@@ -110,6 +113,8 @@ __global__ void __launch_bounds__(kFTPB, 2) k_finish(Ctx c) {
             uint32_t run = 0;
 #pragma unroll
             for (int i = 0; i < kFItems; ++i) {
+                if (i >= nit)
+                    break;
                 const int pos = wid * (32 * kFItems) + i * 32 + lane;
                 const bool valid = pos < len;
                 const unsigned dig = valid ? (unsigned)((unsigned long long)key[i] >> wl) & dmask : 0u;
@@ -147,6 +152,8 @@ __global__ void __launch_bounds__(kFTPB, 2) k_finish(Ctx c) {
             __syncthreads();
 #pragma unroll
             for (int i = 0; i < kFItems; ++i) {
+                if (i >= nit)
+                    break;
                 const int pos = wid * (32 * kFItems) + i * 32 + lane;
                 if (pos < len) {
                     const unsigned dig = (unsigned)((unsigned long long)key[i] >> wl) & dmask;
@@ -158,6 +165,8 @@ __global__ void __launch_bounds__(kFTPB, 2) k_finish(Ctx c) {
             __syncthreads();
 #pragma unroll
             for (int i = 0; i < kFItems; ++i) {
+                if (i >= nit)
+                    break;
                 const int pos = wid * (32 * kFItems) + i * 32 + lane;
                 if (pos < len) {
                     key[i] = s_key[pos];
@@ -290,17 +299,18 @@ __global__ void __launch_bounds__(kRelTPB) k_relink_part(Ctx c, int rb) {
     }
 }
 
-__global__ void k_relink_apply(Ctx c, int rb) {
+// Apply the pairs of node blocks [b0, b0 + nbk): one launch per window so
+// the stores in flight stay inside a few MB of next[].
+__global__ void k_relink_apply(Ctx c, int rb, int b0) {
     if (*(volatile int32_t *)c.status)
         return;
     const int32_t *tv = c.idxb[0], *ts = c.idxb[1];
     unsigned char *next = reinterpret_cast<unsigned char *>(c.desc[0].next);
     const int64_t stride = c.desc[0].next_stride;
-    const int64_t mask = (1ll << rb) - 1;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.ncap; i += (int64_t)gridDim.x * blockDim.x) {
-        if ((i & mask) < c.rel_cursor[i >> rb])
-            *(int32_t *)(next + (int64_t)tv[i] * stride) = ts[i];
-    }
+    const int32_t cnt = c.rel_cursor[b0];
+    const int64_t base = (int64_t)b0 << rb;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        *(int32_t *)(next + (int64_t)tv[base + i] * stride) = ts[base + i];
 }
 
 __global__ void k_empty_roots(Ctx c) {
@@ -340,8 +350,10 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
         const int rb = relink_bucket_bits(c);
         const int64_t pblocks = min((int64_t)sms * 8, max((int64_t)1, (c.ncap + kRelTile - 1) / kRelTile));
         k_relink_part<<<(unsigned)pblocks, kRelTPB, 0, s>>>(c, rb);
-        const int64_t ablocks = min((int64_t)sms * 8, max((int64_t)1, (c.ncap + 255) / 256));
-        k_relink_apply<<<(unsigned)ablocks, 256, 0, s>>>(c, rb);
+        const int64_t ablocks = min((int64_t)sms * 8, (int64_t)(((1ll << rb) + 255) / 256));
+        const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
+        for (int b = 0; b < nb; ++b)
+            k_relink_apply<<<(unsigned)ablocks, 256, 0, s>>>(c, rb, b);
     } else {
         const int64_t blocks = min((int64_t)sms * 16, max((int64_t)1, (c.ncap + 255) / 256));
         k_relink<<<(unsigned)blocks, 256, 0, s>>>(c);

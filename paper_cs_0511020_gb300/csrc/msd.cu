@@ -9,15 +9,26 @@
 // into 2^D sub-segments laid out in ascending digit order, which is the order
 // the ascending concatenation produces.
 //
+// A pass needs, for every tile, where each of its digits starts in the
+// output: the segment's bucket start plus the counts of that digit in the
+// segment's earlier tiles.  Those per-tile counts are produced one step ahead
+// -- by the previous pass while it writes each element (it knows the element's
+// next tile and next digit), or by seg_stats for a segment's first pass -- and
+// turned into prefixes by a two-level scan, so the pass itself has no
+// dependence between tiles and can prefetch its next tile freely.
+//
 // One iteration (= one recursion level for every live segment):
-//   seg_stats     pending segments: 16-bin histogram of the window under
-//                 their top bit and the AND/OR of their keys
+//   seg_stats     pending segments: per-tile counts of the window under their
+//                 top bit, and the AND/OR of their keys
 //   plan_pending  pending -> active / small / done / pending again (when the
 //                 top window does not vary, the segment retries one window
-//                 lower, at its highest varying bit)
-//   pass          per active tile: warp-ballot ranking, decoupled look-back
-//                 over the tiles of its segment, stable scatter through shared
-//                 memory; fused: next-window histogram and AND/OR per bucket
+//                 lower, at its highest varying bit); tile, chunk and
+//                 next-row bases of all active segments
+//   tile_scan     per chunk of 256 tiles: exclusive prefixes of the counts
+//   chunk_scan    per segment: prefixes over its chunks; segment histogram
+//   pass          per tile: warp-ballot ranking, stable scatter through
+//                 shared memory; fused: counts per next-pass tile and AND/OR
+//                 per output bucket
 //   plan_count / plan_scan / plan_write
 //                 output buckets -> next active / pending / small / done
 #include "pbit_internal.cuh"
@@ -26,11 +37,13 @@ namespace pbit {
 
 constexpr int kTPB = 256;             // threads per pass / stats CTA
 constexpr int kItems = 8;             // items per thread in a pass tile
+constexpr int kTileLog = 11;
 constexpr int kTile = kTPB * kItems;  // 2048 elements per pass tile
-constexpr int kStatTile = 8192;       // elements per seg_stats tile
+static_assert(kTile == 1 << kTileLog, "tile is a power of two");
 constexpr int kD = 4;                 // GPU digit width (16 buckets, as the paper's K = 4)
 constexpr int kBins = 1 << kD;
-static_assert(kTPB == kBins * kBins, "the next-window histogram flush maps one thread per counter");
+constexpr int kScanRows = 256;        // tiles per scan chunk (one per thread)
+constexpr int kRowPad = kBins;        // extra next-pass rows per segment (one per bucket)
 
 __host__ __device__ constexpr int tiles_of(int64_t len, int64_t tile) { return (int)((len + tile - 1) / tile); }
 
@@ -69,18 +82,50 @@ __device__ int block_excl_scan(int v, int *total, int *sh /* >= 33 ints */) {
     return r;
 }
 
+// Block-wide exclusive scan of 16-vectors (one per thread, 256 threads):
+// v[] becomes the exclusive prefix, tot[] the block totals (all threads).
+__device__ void block_excl_scan16(uint32_t (&v)[kBins], uint32_t (&tot)[kBins], uint32_t *sh /* 8 x 16 + 16 */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc[kBins];
+#pragma unroll
+    for (int j = 0; j < kBins; ++j) {
+        uint32_t x = v[j];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o)
+                x += y;
+        }
+        inc[j] = x;
+    }
+    if (lane == 31) {
+#pragma unroll
+        for (int j = 0; j < kBins; ++j)
+            sh[wid * kBins + j] = inc[j];
+    }
+    __syncthreads();
+    if (threadIdx.x < kBins) {
+        const int j = threadIdx.x;
+        uint32_t run = 0;
+        for (int w = 0; w < kTPB / 32; ++w) {
+            const uint32_t x = sh[w * kBins + j];
+            sh[w * kBins + j] = run;
+            run += x;
+        }
+        sh[(kTPB / 32) * kBins + j] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kBins; ++j) {
+        v[j] = inc[j] - v[j] + sh[wid * kBins + j];
+        tot[j] = sh[(kTPB / 32) * kBins + j];
+    }
+    __syncthreads();
+}
+
 __device__ __forceinline__ int top_bit(unsigned long long v) { return 63 - __clzll((long long)v); }
 __device__ __forceinline__ unsigned long long low_mask(int bits) {
     return bits >= 64 ? ~0ull : ((1ull << bits) - 1ull);
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // ------------------------------------------------------------- plan_init
@@ -107,7 +152,7 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
         }
         int is_fin = (i < L && n >= 1 && n <= c.cutoff) ? 1 : 0;
         int is_pend = (i < L && n > c.cutoff) ? 1 : 0;
-        int tiles = is_pend ? tiles_of(n, kStatTile) : 0;
+        int tiles = is_pend ? tiles_of(n, kTile) : 0;
         int tf, tp, tt;
         int pf = block_excl_scan(is_fin, &tf, sh);
         int pp = block_excl_scan(is_pend, &tp, sh);
@@ -122,7 +167,7 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
         if (is_pend) {
             int k = s_pend_base + pp;
             if (k < c.seg_cap) {
-                c.pend[0][k] = Seg{start, n, 0, (int16_t)c.M, 0};
+                c.pend[0][k] = Seg{start, n, 0, (int16_t)c.M, 0, 0, 0};
                 c.pend_tile_base[0][k] = s_tile_base + pt;
             } else {
                 set_status(c.status, kStOverflow);
@@ -143,15 +188,18 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
             c.pend_tile_base[0][s_pend_base] = s_tile_base;
         c.ctr->stat_tiles[0] = s_tile_base;
         c.ctr->act_count[0] = 0;
+        c.ctr->brows[0] = 0;
+        if (s_tile_base > c.row_cap)
+            set_status(c.status, kStOverflow);
     }
 }
 
 // ------------------------------------------------------------- seg_stats
-// Histogram of the window [max(hi-D,0), hi) and AND/OR of every pending
-// segment, 8 keys per thread in flight.
+// For every pass tile of every pending segment: the counts of the digits in
+// the window [max(hi-D,0), hi) (plain stores into its tcnt row, placed after
+// the rows the previous pass filled), and the AND/OR of the segment's keys.
 template <typename KeyT>
 __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
-    constexpr int kU = 8;
     __shared__ uint32_t s_cnt[kBins];
     __shared__ unsigned long long s_and, s_or;
     __shared__ int s_tile;
@@ -160,6 +208,7 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
     const int cur = it & 1;
     const int P = c.ctr->pend_count[cur];
     const int ntiles = c.ctr->stat_tiles[cur];
+    const int rbase = c.ctr->brows[cur];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (threadIdx.x < kBins)
         s_cnt[threadIdx.x] = 0;
@@ -178,39 +227,37 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         const int s = upper_index(c.pend_tile_base[cur], P, g);
         const Seg sg = c.pend[cur][s];
         const int k = g - c.pend_tile_base[cur][s];
-        const int64_t b0 = (int64_t)sg.start + (int64_t)k * kStatTile;
-        const int cnt = (int)min((int64_t)kStatTile, (int64_t)sg.start + sg.len - b0);
+        const int64_t b0 = (int64_t)sg.start + (int64_t)k * kTile;
+        const int cnt = (int)min((int64_t)kTile, (int64_t)sg.start + sg.len - b0);
         const KeyT *keys = reinterpret_cast<const KeyT *>(c.keyb[sg.buf & 1]);
         const int hi = sg.hi, lo = max(hi - kD, 0);
         const unsigned dmask = (1u << (hi - lo)) - 1u;
         if (threadIdx.x == 0)
             atomicAdd((unsigned long long *)&c.ctr->stat_elems[it], (unsigned long long)cnt);
+        unsigned long long kv[kItems];
+#pragma unroll
+        for (int u = 0; u < kItems; ++u) {
+            const int pos = wid * 32 * kItems + u * 32 + lane;
+            kv[u] = pos < cnt ? (unsigned long long)keys[b0 + pos] : 0ull;
+        }
         uint32_t wc = 0;
         unsigned long long a_and = ~0ull, a_or = 0ull;
-        for (int base = wid * 32 * kU; base < cnt; base += kTPB * kU) {
-            unsigned long long kv[kU];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int pos = base + u * 32 + lane;
-                kv[u] = pos < cnt ? (unsigned long long)keys[b0 + pos] : 0ull;
+        for (int u = 0; u < kItems; ++u) {
+            const int pos = wid * 32 * kItems + u * 32 + lane;
+            const bool valid = pos < cnt;
+            if (valid) {
+                a_and &= kv[u];
+                a_or |= kv[u];
             }
+            const unsigned dig = (unsigned)(kv[u] >> lo) & dmask;
+            unsigned m = __ballot_sync(kFull, valid);
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int pos = base + u * 32 + lane;
-                const bool valid = pos < cnt;
-                if (valid) {
-                    a_and &= kv[u];
-                    a_or |= kv[u];
-                }
-                const unsigned dig = (unsigned)(kv[u] >> lo) & dmask;
-                unsigned m = __ballot_sync(kFull, valid);
-#pragma unroll
-                for (int b = 0; b < kD; ++b) {
-                    const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
-                    m &= ((lane >> b) & 1) ? bb : ~bb;
-                }
-                wc += __popc(m);
+            for (int b = 0; b < kD; ++b) {
+                const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
+                m &= ((lane >> b) & 1) ? bb : ~bb;
             }
+            wc += __popc(m);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -225,11 +272,10 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         }
         __syncthreads();
         if (threadIdx.x < kBins) {
-            const uint32_t v = s_cnt[threadIdx.x];
-            if (v) {
-                atomicAdd(&c.phist[cur][(int64_t)s * kBins + threadIdx.x], v);
-                s_cnt[threadIdx.x] = 0;
-            }
+            const int64_t row = (int64_t)rbase + g;
+            if (row < c.row_cap)
+                c.tcnt[cur][row * kBins + threadIdx.x] = s_cnt[threadIdx.x];
+            s_cnt[threadIdx.x] = 0;
         }
         if (threadIdx.x == 0) {
             atomicAnd(&c.pand[cur][s], s_and);
@@ -243,23 +289,26 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
 // ---------------------------------------------------------- plan_pending
 __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
     __shared__ int sh[40];
-    __shared__ int s_act_base, s_re_base, s_re_tiles, s_tile_base;
+    __shared__ int s_act_base, s_re_base, s_re_tiles, s_tile_base, s_chunk_base, s_nrow_base;
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1, nxt = cur ^ 1;
     const int P = c.ctr->pend_count[cur];
+    const int rbase = c.ctr->brows[cur];
     if (threadIdx.x == 0) {
         s_act_base = c.ctr->act_count[cur];
         s_re_base = 0;
         s_re_tiles = 0;
         s_tile_base = 0;
+        s_chunk_base = 0;
+        s_nrow_base = 0;
     }
     __syncthreads();
     int fin_total = 0;
     for (int r0 = 0; r0 < P; r0 += blockDim.x) {
         const int s = r0 + threadIdx.x;
         int kind = 0;  // 1 fin copy, 2 fin sort, 3 active, 4 pending again
-        Seg sg{0, 0, 0, 0, 0};
+        Seg sg{0, 0, 0, 0, 0, 0, 0};
         int t = 0;
         if (s < P) {
             sg = c.pend[cur][s];
@@ -274,7 +323,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
                     kind = (t >= sg.hi - kD) ? 3 : 4;
             }
         }
-        const int tiles = kind == 4 ? tiles_of(sg.len, kStatTile) : 0;
+        const int tiles = kind == 4 ? tiles_of(sg.len, kTile) : 0;
         int tf, ta, tr, tt;
         const int pf = block_excl_scan(kind == 1 || kind == 2, &tf, sh);
         const int pa = block_excl_scan(kind == 3, &ta, sh);
@@ -288,30 +337,21 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
                 set_status(c.status, kStOverflow);
         } else if (kind == 3) {
             const int64_t a = (int64_t)s_act_base + pa;
-            if (a < c.seg_cap) {
-                c.act[cur][a] = Seg{sg.start, sg.len, (int16_t)max(sg.hi - kD, 0), sg.hi, sg.buf};
-                const uint32_t *src = c.phist[cur] + (int64_t)s * kBins;
-                uint32_t *dst = c.act_hist[cur] + a * kBins;
-                for (int b = 0; b < kBins; ++b)
-                    dst[b] = src[b];
-            } else {
+            if (a < c.seg_cap)
+                c.act[cur][a] = Seg{sg.start, sg.len, (int16_t)max(sg.hi - kD, 0), sg.hi, sg.buf,
+                                    rbase + c.pend_tile_base[cur][s], 0};
+            else
                 set_status(c.status, kStOverflow);
-            }
         } else if (kind == 4) {
             const int64_t r = (int64_t)s_re_base + pr;
             if (r < c.seg_cap) {
-                c.pend[nxt][r] = Seg{sg.start, sg.len, 0, (int16_t)(t + 1), sg.buf};
+                c.pend[nxt][r] = Seg{sg.start, sg.len, 0, (int16_t)(t + 1), sg.buf, 0, 0};
                 c.pend_tile_base[nxt][r] = s_re_tiles + pt;
             } else {
                 set_status(c.status, kStOverflow);
             }
         }
-        if (s < P) {  // leave the stats row clean for its next use
-            uint4 *row = reinterpret_cast<uint4 *>(c.phist[cur] + (int64_t)s * kBins);
-            row[0] = make_uint4(0, 0, 0, 0);
-            row[1] = make_uint4(0, 0, 0, 0);
-            row[2] = make_uint4(0, 0, 0, 0);
-            row[3] = make_uint4(0, 0, 0, 0);
+        if (s < P) {  // leave the AND/OR slots clean for their next use
             c.pand[cur][s] = ~0ull;
             c.por[cur][s] = 0ull;
         }
@@ -331,26 +371,36 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
         c.ctr->stat_tiles[nxt] = s_re_tiles;
     }
     __syncthreads();
-    // tile bases of all active segments of this pass
+    // tile, scan-chunk and next-row bases of all active segments of this pass
     const int A = (int)min((int64_t)s_act_base, c.seg_cap);
     long long my_elems = 0, my_final = 0;
     for (int r0 = 0; r0 < A; r0 += blockDim.x) {
         const int a = r0 + threadIdx.x;
-        int tiles = 0;
+        int tiles = 0, chunks = 0, nrows = 0;
         if (a < A) {
             const Seg sa = c.act[cur][a];
             tiles = tiles_of(sa.len, kTile);
+            chunks = tiles_of(tiles, kScanRows);
+            nrows = sa.lo > 0 ? tiles + kRowPad : 0;
             my_elems += sa.len;
             if (sa.lo == 0)
                 my_final += sa.len;
         }
-        int tt;
+        int tt, tc, tn;
         const int pt = block_excl_scan(tiles, &tt, sh);
-        if (a < A)
+        const int pc = block_excl_scan(chunks, &tc, sh);
+        const int pn = block_excl_scan(nrows, &tn, sh);
+        if (a < A) {
             c.act_tile_base[cur][a] = s_tile_base + pt;
+            c.act_chunk_base[cur][a] = s_chunk_base + pc;
+            c.act_nrow_base[cur][a] = s_nrow_base + pn;
+        }
         __syncthreads();
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             s_tile_base += tt;
+            s_chunk_base += tc;
+            s_nrow_base += tn;
+        }
         __syncthreads();
     }
     if (my_elems) {
@@ -359,9 +409,112 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
     }
     if (threadIdx.x == 0) {
         c.act_tile_base[cur][A] = s_tile_base;
-        if (s_tile_base > c.tile_cap)
+        c.act_chunk_base[cur][A] = s_chunk_base;
+        c.act_nrow_base[cur][A] = s_nrow_base;
+        if (s_tile_base > c.tile_cap || s_chunk_base > c.scan_cap || s_nrow_base + c.ctr->stat_tiles[nxt] > c.row_cap)
             set_status(c.status, kStOverflow);
         c.ctr->num_tiles[cur] = (int32_t)min((int64_t)s_tile_base, c.tile_cap);
+        c.ctr->num_chunks[cur] = (int32_t)min((int64_t)s_chunk_base, c.scan_cap);
+        c.ctr->brows[nxt] = s_nrow_base;
+    }
+}
+
+// ------------------------------------------------------------- tile_scan
+// Zero the next pass's count rows; then, per chunk of 256 tiles of an active
+// segment, replace each tile's counts by the exclusive prefix within the
+// chunk and record the chunk totals.
+__global__ void __launch_bounds__(kTPB) k_tile_scan(Ctx c, int it) {
+    __shared__ uint32_t sh[(kTPB / 32 + 1) * kBins];
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1, nxt = cur ^ 1;
+    {
+        const int64_t words = (int64_t)c.ctr->brows[nxt] * kBins / 4;
+        uint4 *z = reinterpret_cast<uint4 *>(c.tcnt[nxt]);
+        for (int64_t i = (int64_t)blockIdx.x * kTPB + threadIdx.x; i < words; i += (int64_t)gridDim.x * kTPB)
+            z[i] = make_uint4(0, 0, 0, 0);
+    }
+    const int A = c.ctr->act_count[cur];
+    const int nch = c.ctr->num_chunks[cur];
+    for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int a = upper_index(c.act_chunk_base[cur], A, ch);
+        const Seg sg = c.act[cur][a];
+        const int lc = ch - c.act_chunk_base[cur][a];
+        const int nt = c.act_tile_base[cur][a + 1] - c.act_tile_base[cur][a];
+        const int t = lc * kScanRows + threadIdx.x;
+        uint32_t v[kBins], tot[kBins];
+        uint4 *row = reinterpret_cast<uint4 *>(c.tcnt[cur] + ((int64_t)sg.row + t) * kBins);
+        if (t < nt) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 x = row[q];
+                v[4 * q] = x.x;
+                v[4 * q + 1] = x.y;
+                v[4 * q + 2] = x.z;
+                v[4 * q + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kBins; ++j)
+                v[j] = 0;
+        }
+        block_excl_scan16(v, tot, sh);
+        if (t < nt) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                row[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        if (threadIdx.x < kBins)
+            c.ctot[(int64_t)ch * kBins + threadIdx.x] = tot[threadIdx.x];
+    }
+}
+
+// ------------------------------------------------------------ chunk_scan
+// Per active segment: exclusive prefixes over its chunks (in place) and the
+// segment's digit histogram.
+__global__ void __launch_bounds__(kTPB) k_chunk_scan(Ctx c, int it) {
+    __shared__ uint32_t sh[(kTPB / 32 + 1) * kBins];
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1;
+    const int A = c.ctr->act_count[cur];
+    for (int a = blockIdx.x; a < A; a += gridDim.x) {
+        const int c0 = c.act_chunk_base[cur][a], c1 = c.act_chunk_base[cur][a + 1];
+        uint32_t base[kBins];
+#pragma unroll
+        for (int j = 0; j < kBins; ++j)
+            base[j] = 0;
+        for (int b = c0; b < c1; b += kTPB) {
+            const int ch = b + threadIdx.x;
+            uint32_t v[kBins], tot[kBins];
+            uint4 *row = reinterpret_cast<uint4 *>(c.ctot + (int64_t)ch * kBins);
+            if (ch < c1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 x = row[q];
+                    v[4 * q] = x.x;
+                    v[4 * q + 1] = x.y;
+                    v[4 * q + 2] = x.z;
+                    v[4 * q + 3] = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kBins; ++j)
+                    v[j] = 0;
+            }
+            block_excl_scan16(v, tot, sh);
+            if (ch < c1) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    row[q] = make_uint4(v[4 * q] + base[4 * q], v[4 * q + 1] + base[4 * q + 1],
+                                        v[4 * q + 2] + base[4 * q + 2], v[4 * q + 3] + base[4 * q + 3]);
+            }
+#pragma unroll
+            for (int j = 0; j < kBins; ++j)
+                base[j] += tot[j];
+        }
+        if (threadIdx.x < kBins)
+            c.act_hist[cur][(int64_t)a * kBins + threadIdx.x] = base[threadIdx.x];
     }
 }
 
@@ -371,10 +524,13 @@ struct PassSmem {
     uint32_t tile_off[kBins + 1];
     uint32_t tile_cnt[kBins];
     int32_t gbase[kBins];
-    uint32_t nh[kBins * kBins];
-    int32_t g, seg, cnt, k, shk, shi;
-    int32_t err;
-    alignas(8) uint64_t bar;
+    int32_t bstart[kBins];            // start of each output bucket
+    int32_t nrow[kBins];              // first next-pass row of each output bucket
+    int32_t k0[kBins];                // next-pass tile of this tile's first element per bucket
+    uint32_t nc[kBins * 2 * kBins];   // counts per (bucket, next tile k0/k0+1, next digit)
+    int32_t st_seg[2], st_cnt[2], st_k[2], st_shk[2], st_shi[2];
+    int32_t nt[2];
+    alignas(8) uint64_t bar[2];
 };
 
 template <typename KeyT>
@@ -383,14 +539,14 @@ struct PassLayout {
     static constexpr int kIdxBytes = kTile * 4 + 32;
     static constexpr int kStage = ((kKeyBytes + kIdxBytes + 127) / 128) * 128;
     static constexpr int kHdr = ((int)sizeof(PassSmem) + 127) / 128 * 128;
-    static constexpr int kTotal = kHdr + kStage;
+    static constexpr int kTotal = kHdr + 2 * kStage;
     static constexpr int kMinBlocks = sizeof(KeyT) == 8 ? 3 : 4;
 };
 
-// Issue the bulk copies of tile g into the stage buffer (one thread).
+// Issue the bulk copies of tile g into stage st (one thread).
 template <typename KeyT>
-__device__ __forceinline__ void pass_issue(const Ctx &c, int cur, int g, PassSmem &S, unsigned char *stage,
-                                           int A) {
+__device__ __forceinline__ void pass_issue(const Ctx &c, int cur, int g, int st, PassSmem &S,
+                                           unsigned char *stage, int A) {
     const int s = upper_index(c.act_tile_base[cur], A, g);
     const Seg sg = c.act[cur][s];
     const int k = g - c.act_tile_base[cur][s];
@@ -401,87 +557,38 @@ __device__ __forceinline__ void pass_issue(const Ctx &c, int cur, int g, PassSme
     const unsigned char *ib = reinterpret_cast<const unsigned char *>(c.idxb[sg.buf & 1]);
     const int64_t k_lo = (start * W) & ~15ll, k_hi = ((start + cnt) * W + 15) & ~15ll;
     const int64_t i_lo = (start * 4) & ~15ll, i_hi = ((start + cnt) * 4 + 15) & ~15ll;
-    S.seg = s;
-    S.cnt = cnt;
-    S.k = k;
-    S.shk = (int32_t)((start * W - k_lo) / W);
-    S.shi = (int32_t)((start * 4 - i_lo) / 4);
+    S.st_seg[st] = s;
+    S.st_cnt[st] = cnt;
+    S.st_k[st] = k;
+    S.st_shk[st] = (int32_t)((start * W - k_lo) / W);
+    S.st_shi[st] = (int32_t)((start * 4 - i_lo) / 4);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(&S.bar, (uint32_t)((k_hi - k_lo) + (i_hi - i_lo)));
-    bulk_g2s(stage, kb + k_lo, (uint32_t)(k_hi - k_lo), &S.bar);
-    bulk_g2s(stage + PassLayout<KeyT>::kKeyBytes, ib + i_lo, (uint32_t)(i_hi - i_lo), &S.bar);
+    mbar_arrive_expect_tx(&S.bar[st], (uint32_t)((k_hi - k_lo) + (i_hi - i_lo)));
+    bulk_g2s(stage, kb + k_lo, (uint32_t)(k_hi - k_lo), &S.bar[st]);
+    bulk_g2s(stage + PassLayout<KeyT>::kKeyBytes, ib + i_lo, (uint32_t)(i_hi - i_lo), &S.bar[st]);
 }
 
-// Warp 0: walk back over the earlier tiles of the segment until every digit
-// has met an inclusive prefix (this tile's own aggregate was published
-// already).  The warp stays converged (one 128-byte read of 16 words per
-// step); a word is (epoch, state, count) in one 64-bit store, so relaxed
-// accesses suffice.
-__device__ __forceinline__ uint32_t lookback(const Ctx &c, int g0, uint32_t tot, uint32_t epoch, int lane,
-                                             int *err) {
-    const int d = lane & (kBins - 1);
-    const bool owner = lane < kBins;
-    uint32_t excl = 0;
-    bool done = !owner;
-    int gp = g0 - 1;
-    uint64_t t0 = 0;
-    long long spins = 0;
-    while (true) {
-        unsigned long long x = 0;
-        bool ready = true;
-        if (!done) {
-            x = ld_relaxed_u64(c.lb + (int64_t)gp * kBins + d);
-            ready = ((uint32_t)(x >> 56) == (epoch & 0xff)) && (((x >> 54) & 3ull) != 0);
-        }
-        if (!__all_sync(kFull, ready)) {
-            if (++spins == 1)
-                t0 = globaltimer_ns();
-            if ((spins & 15) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
-                *err = 1;
-                break;
-            }
-            continue;
-        }
-        spins = 0;
-        if (!done) {
-            excl += (uint32_t)(x & ((1ull << 54) - 1));
-            done = ((x >> 54) & 3ull) == kLbIncl;
-        }
-        if (__all_sync(kFull, done))
-            break;
-        --gp;
-    }
-    if (owner)
-        st_relaxed_u64(c.lb + (int64_t)g0 * kBins + d, lb_pack(epoch, kLbIncl, (unsigned long long)excl + tot));
-    return excl;
-}
-
-// One CTA works on one tile at a time (tile ids taken in order from a
-// counter, so every earlier tile of the segment is already being processed);
-// several CTAs per SM overlap each other's loads, look-backs and stores.
+// Persistent CTAs take tiles from a counter and double-buffer them: the bulk
+// copy of the next tile is in flight while the current one is ranked and
+// written.  Tiles are independent: every tile reads its digits' output
+// positions from the scanned counts.
 template <typename KeyT>
 __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx c, int it) {
     extern __shared__ __align__(128) unsigned char smem[];
     PassSmem &S = *reinterpret_cast<PassSmem *>(smem);
-    unsigned char *stage = smem + PassLayout<KeyT>::kHdr;
+    unsigned char *stages = smem + PassLayout<KeyT>::kHdr;
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1, nxt = cur ^ 1;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned lt = lanemask_lt();
-    const uint32_t epoch = (uint32_t)it + 1;
 
-    // clear the other parity's bucket accumulators (consumed by the last plan)
+    // reset the other parity's bucket AND/OR (consumed by the last plan)
     {
         const int64_t rows = (int64_t)c.ctr->act_count[nxt] * kBins;
         for (int64_t r = (int64_t)blockIdx.x * kTPB + tid; r < rows; r += (int64_t)gridDim.x * kTPB) {
             c.band[nxt][r] = ~0ull;
             c.bor[nxt][r] = 0ull;
-            uint4 *z = reinterpret_cast<uint4 *>(c.nh[nxt] + r * kBins);
-            z[0] = make_uint4(0, 0, 0, 0);
-            z[1] = make_uint4(0, 0, 0, 0);
-            z[2] = make_uint4(0, 0, 0, 0);
-            z[3] = make_uint4(0, 0, 0, 0);
         }
     }
     const int A = c.ctr->act_count[cur];
@@ -490,40 +597,74 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
         return;
 
     if (tid == 0) {
-        mbar_init(&S.bar, 1);
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
         fence_mbar_init();
-        S.err = 0;
     }
-    S.nh[tid] = 0;
+    for (int i = tid; i < kBins * 2 * kBins; i += kTPB)
+        S.nc[i] = 0;
+    uint32_t phase[2] = {0, 0};
+    int st = 0;
+    if (tid == 0) {
+        const int g = atomicAdd(&c.ctr->tile_ctr[it], 1);
+        S.nt[0] = g;
+        if (g < ntiles)
+            pass_issue<KeyT>(c, cur, g, 0, S, stages, A);
+    }
     __syncthreads();
-    uint32_t phase = 0;
-    while (true) {
-        if (tid == 0) {
-            const int g = atomicAdd(&c.ctr->tile_ctr[it], 1);
-            S.g = g;
-            if (g < ntiles)
-                pass_issue<KeyT>(c, cur, g, S, stage, A);
+    int g = S.nt[0];
+    while (g < ntiles) {
+        unsigned char *stage = stages + st * PassLayout<KeyT>::kStage;
+        if (tid == 0) {  // prefetch the next tile into the other stage
+            const int g2 = atomicAdd(&c.ctr->tile_ctr[it], 1);
+            S.nt[st ^ 1] = g2;
+            if (g2 < ntiles)
+                pass_issue<KeyT>(c, cur, g2, st ^ 1, S, stages + (st ^ 1) * PassLayout<KeyT>::kStage, A);
         }
-        __syncthreads();
-        const int g = S.g;
-        if (g >= ntiles)
-            break;
-        const bool landed = mbar_wait_bounded(&S.bar, phase, 1ll << 26);
-        if (!__syncthreads_and(landed)) {
-            set_status(c.status, PBIT_ETIMEOUT);
-            if (tid == 0)  // wait (bounded) for the copy still in flight before leaving
-                mbar_wait_bounded(&S.bar, phase, 1ll << 26);
-            return;
-        }
-        phase ^= 1;
-        const int s = S.seg;
-        const int k = S.k;
-        const int cnt = S.cnt;
+        // per-tile output bases (warp 1; overlaps the copy wait of the others)
+        const int s = S.st_seg[st];
+        const int k = S.st_k[st];
+        const int cnt = S.st_cnt[st];
         const Seg sg = c.act[cur][s];
         const int lo = sg.lo, hi = sg.hi;
+        if (wid == 1 && lane < kBins) {
+            const int d = lane;
+            const uint32_t h = c.act_hist[cur][(int64_t)s * kBins + d];
+            uint32_t ex = h;  // exclusive prefix over digits of the segment histogram
+            uint32_t nt_d = (uint32_t)tiles_of(h, kTile);
+#pragma unroll
+            for (int o = 1; o < kBins; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffu, ex, o);
+                const uint32_t z = __shfl_up_sync(0xffffu, nt_d, o);
+                if (d >= o) {
+                    ex += y;
+                    nt_d += z;
+                }
+            }
+            ex -= h;
+            nt_d -= (uint32_t)tiles_of(h, kTile);
+            const int ch = c.act_chunk_base[cur][s] + k / kScanRows;
+            const uint32_t before = c.ctot[(int64_t)ch * kBins + d] +
+                                    c.tcnt[cur][((int64_t)sg.row + k) * kBins + d];
+            S.bstart[d] = sg.start + (int32_t)ex;
+            S.gbase[d] = sg.start + (int32_t)ex + (int32_t)before;
+            S.k0[d] = (int32_t)(before >> kTileLog);
+            S.nrow[d] = c.act_nrow_base[cur][s] + (int32_t)nt_d;
+        }
+        const bool landed = mbar_wait_bounded(&S.bar[st], phase[st], 1ll << 26);
+        if (!__syncthreads_and(landed)) {
+            set_status(c.status, PBIT_ETIMEOUT);
+            if (tid == 0) {  // wait (bounded) for the copies still in flight before leaving
+                mbar_wait_bounded(&S.bar[st], phase[st], 1ll << 26);
+                if (S.nt[st ^ 1] < ntiles)
+                    mbar_wait_bounded(&S.bar[st ^ 1], phase[st ^ 1], 1ll << 26);
+            }
+            return;
+        }
+        phase[st] ^= 1;
         const unsigned dmask = (1u << (hi - lo)) - 1u;
-        const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + S.shk;
-        const int32_t *si = reinterpret_cast<const int32_t *>(stage + PassLayout<KeyT>::kKeyBytes) + S.shi;
+        const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + S.st_shk[st];
+        const int32_t *si = reinterpret_cast<const int32_t *>(stage + PassLayout<KeyT>::kKeyBytes) + S.st_shi[st];
 
         // ---- load + warp-ballot ranking (order: warp, item, lane == memory order)
         KeyT key[kItems];
@@ -551,10 +692,9 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
         if (lane < kBins)
             S.wcnt[wid][lane] = run;
         __syncthreads();
-        // ---- tile histogram and prefixes; publish this tile's aggregate
-        uint32_t tot = 0;
-        if (wid == 0) {
+        if (wid == 0) {  // tile histogram and prefixes
             const int d = lane & (kBins - 1);
+            uint32_t tot = 0;
             if (lane < kBins) {
 #pragma unroll
                 for (int w = 0; w < kTPB / 32; ++w) {
@@ -575,7 +715,6 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                 S.tile_off[d] = incl - tot;
                 if (d == kBins - 1)
                     S.tile_off[kBins] = incl;
-                st_relaxed_u64(c.lb + (int64_t)g * kBins + d, lb_pack(epoch, k == 0 ? kLbIncl : kLbAgg, tot));
             }
         }
         __syncthreads();
@@ -592,27 +731,8 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                 oi[lp] = idx[i];
             }
         }
-        // ---- look-back (warp 0) overlaps the other warps' scatter
-        if (wid == 0) {
-            int err = 0;
-            const uint32_t excl = (k == 0) ? 0u : lookback(c, g, tot, epoch, lane, &err);
-            if (lane < kBins) {
-                const int d = lane;
-                uint32_t bex = 0;
-                const uint32_t *h = c.act_hist[cur] + (int64_t)s * kBins;
-                for (int b = 0; b < d; ++b)
-                    bex += h[b];
-                S.gbase[d] = sg.start + (int32_t)bex + (int32_t)excl;
-            }
-            if (err && lane == 0) {
-                set_status(c.status, PBIT_ETIMEOUT);
-                S.err = 1;
-            }
-        }
         __syncthreads();
-        if (S.err)  // a look-back gave up: write nothing
-            return;
-        // ---- coalesced write-out (+ next-window histogram)
+        // ---- coalesced write-out (+ counts of the next pass's tiles)
         const int seg_end = sg.start + sg.len;
         KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(sg.buf & 1) ^ 1]);
         int32_t *oidx = c.idxb[(sg.buf & 1) ^ 1];
@@ -640,7 +760,8 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                 okey[dst] = kk;
                 oidx[dst] = oi[j];
                 const unsigned nd = (unsigned)((unsigned long long)kk >> nlo) & nmask;
-                atomicAdd(&S.nh[dig * kBins + nd], 1u);
+                const int kk1 = ((dst - S.bstart[dig]) >> kTileLog) - S.k0[dig];  // 0 or 1
+                atomicAdd(&S.nc[(dig * 2 + kk1) * kBins + nd], 1u);
             }
             // AND/OR of every output bucket: warp wid handles digits wid, wid+8
             for (int d = wid; d < kBins; d += kTPB / 32) {
@@ -665,13 +786,22 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                 }
             }
             __syncthreads();
-            const uint32_t v = S.nh[tid];
-            if (v) {
-                atomicAdd(&c.nh[cur][(int64_t)s * kBins * kBins + tid], v);
-                S.nh[tid] = 0;
+            for (int i = tid; i < kBins * 2 * kBins; i += kTPB) {
+                const uint32_t v = S.nc[i];
+                if (v) {
+                    const int d = i / (2 * kBins), kk1 = (i / kBins) & 1, nd = i % kBins;
+                    const int64_t row = (int64_t)S.nrow[d] + S.k0[d] + kk1;
+                    if (row < c.row_cap)
+                        atomicAdd(&c.tcnt[nxt][row * kBins + nd], v);
+                    else
+                        set_status(c.status, kStOverflow);
+                    S.nc[i] = 0;
+                }
             }
         }
         __syncthreads();
+        g = S.nt[st ^ 1];
+        st ^= 1;
     }
 }
 
@@ -710,7 +840,7 @@ __global__ void k_plan_count(Ctx c, int it) {
             na += kd == 3;
             np += kd == 4;
             nf += (kd == 1 || kd == 2);
-            nt += (kd == 4) ? tiles_of(cnt, kStatTile) : 0;
+            nt += (kd == 4) ? tiles_of(cnt, kTile) : 0;
         }
         c.plan_cnt[s] = make_int4(na, np, nf, nt);
     }
@@ -751,7 +881,7 @@ __global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        if (s_a > c.seg_cap || s_p > c.seg_cap || s_f > c.fin_cap)
+        if (s_a > c.seg_cap || s_p > c.seg_cap || s_f > c.fin_cap || c.ctr->brows[nxt] + s_t > c.row_cap)
             set_status(c.status, kStOverflow);
         c.ctr->act_count[nxt] = (int32_t)min((int64_t)s_a, c.seg_cap);
         c.ctr->pend_count[nxt] = (int32_t)min((int64_t)s_p, c.seg_cap);
@@ -773,6 +903,7 @@ __global__ void k_plan_write(Ctx c, int it) {
         int64_t a = o.x, p = o.y, f = o.z, tb = o.w;
         const uint32_t *h = c.act_hist[cur] + (int64_t)s * kBins;
         int32_t bstart = sg.start;
+        int32_t nrow = c.act_nrow_base[cur][s];
         for (int d = 0; d < kBins; ++d) {
             int t = 0;
             const uint32_t cnt = h[d];
@@ -783,25 +914,20 @@ __global__ void k_plan_write(Ctx c, int it) {
                                    ((kd == 2 ? 1 : 0) << 8) | ((sg.buf & 1) ^ 1)};
                 ++f;
             } else if (kd == 3) {
-                if (a < c.seg_cap) {
-                    c.act[nxt][a] = Seg{bstart, (int32_t)cnt, (int16_t)max(sg.lo - kD, 0), sg.lo, (sg.buf & 1) ^ 1};
-                    const uint4 *src = reinterpret_cast<const uint4 *>(c.nh[cur] + ((int64_t)s * kBins + d) * kBins);
-                    uint4 *dst = reinterpret_cast<uint4 *>(c.act_hist[nxt] + a * kBins);
-                    dst[0] = src[0];
-                    dst[1] = src[1];
-                    dst[2] = src[2];
-                    dst[3] = src[3];
-                }
+                if (a < c.seg_cap)
+                    c.act[nxt][a] = Seg{bstart, (int32_t)cnt, (int16_t)max(sg.lo - kD, 0), sg.lo,
+                                        (sg.buf & 1) ^ 1, nrow, 0};
                 ++a;
             } else if (kd == 4) {
                 if (p < c.seg_cap) {
-                    c.pend[nxt][p] = Seg{bstart, (int32_t)cnt, 0, (int16_t)(t + 1), (sg.buf & 1) ^ 1};
+                    c.pend[nxt][p] = Seg{bstart, (int32_t)cnt, 0, (int16_t)(t + 1), (sg.buf & 1) ^ 1, 0, 0};
                     c.pend_tile_base[nxt][p] = (int32_t)tb;
                 }
-                tb += tiles_of(cnt, kStatTile);
+                tb += tiles_of(cnt, kTile);
                 ++p;
             }
             bstart += (int32_t)cnt;
+            nrow += tiles_of(cnt, kTile);
         }
     }
 }
@@ -817,6 +943,9 @@ static void launch_iter_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     prof_mark("seg_stats", s);
     k_plan_pending<<<1, 1024, 0, s>>>(c, it);
     prof_mark("plan", s);
+    k_tile_scan<<<sms * 4, kTPB, 0, s>>>(c, it);
+    k_chunk_scan<<<sms * 2, kTPB, 0, s>>>(c, it);
+    prof_mark("scan", s);
     k_pass<KeyT><<<sms * per_sm, kTPB, smem, s>>>(c, it);
     prof_mark("pass", s);
     k_plan_count<<<pblocks, 256, 0, s>>>(c, it);
@@ -839,9 +968,11 @@ void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms) {
     }
 }
 
-int64_t launches_per_iteration() { return 6; }
+int64_t launches_per_iteration() { return 8; }
 int pass_tile() { return kTile; }
-int stat_tile() { return kStatTile; }
+int stat_tile() { return kTile; }
 int digit_bits() { return kD; }
+int scan_rows() { return kScanRows; }
+int row_pad() { return kRowPad; }
 
 }  // namespace pbit

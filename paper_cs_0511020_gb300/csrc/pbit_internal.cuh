@@ -40,6 +40,8 @@ struct Seg {
     int16_t lo;
     int16_t hi;
     int32_t buf;
+    int32_t row;  // first row of its per-tile digit counts (tcnt)
+    int32_t pad;
 };
 
 // A finished-or-small run: mode 0 = copy the node ids to the final buffer,
@@ -65,6 +67,8 @@ struct Counters {
     int32_t stat_tiles[2];
     int32_t task_next;         // work counter of the ranking walk
     int32_t pad0;
+    int32_t brows[2];          // tcnt rows handed to the previous pass's buckets
+    int32_t num_chunks[2];     // scan chunks of the pass
     // element counts for the per-kernel algorithmic-byte accounting
     long long pass_elems[kMaxIters];
     long long pass_final_elems[kMaxIters];
@@ -116,12 +120,16 @@ struct Ctx {
     Seg *act[2];
     uint32_t *act_hist[2];      // seg_cap x 16 : histogram of the pass window
     int32_t *act_tile_base[2];  // seg_cap + 1
-    uint32_t *nh[2];            // seg_cap x 16 x 16 : next-window histogram per bucket
+    int32_t *act_chunk_base[2]; // seg_cap + 1 : first scan chunk of the segment
+    int32_t *act_nrow_base[2];  // seg_cap + 1 : first tcnt row of its buckets in the next pass
+    uint32_t *tcnt[2];          // row_cap x 16 : digit counts per pass tile -> exclusive prefixes
+    uint32_t *ctot;             // scan_cap x 16 : per scan chunk totals -> exclusive prefixes
+    int64_t row_cap;
+    int64_t scan_cap;
     unsigned long long *band[2];// seg_cap x 16
     unsigned long long *bor[2];
     Seg *pend[2];
     int32_t *pend_tile_base[2];
-    uint32_t *phist[2];         // seg_cap x 16 bins (window under hi)
     unsigned long long *pand[2];
     unsigned long long *por[2];
     int4 *plan_cnt;             // seg_cap per-segment counts -> offsets
@@ -306,5 +314,7 @@ int relink_max_buckets();
 int pass_tile();
 int stat_tile();
 int digit_bits();
+int scan_rows();
+int row_pad();
 
 }  // namespace pbit
