@@ -8,6 +8,7 @@
 // pool size, the number of lists, the key width and the tune; no call
 // allocates device memory.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <unordered_map>

@@ -1,95 +1,69 @@
 // finish.cu -- stages (c) and (d).
 //
-// (c) Small buckets are finished in shared memory.  In the paper the
-//     recursion runs every bucket down to M == 0 and merge() then appends the
-//     leaf buckets (Sec. "Implementation in C++", Sec. 5.1); the paper itself
-//     notes that MSD sorting spends too long on small chunks (Sec.
-//     "Differences between Pbit and other algorithms sorting with bit key").
-//     Here a bucket of at most `cutoff` nodes is loaded once, sorted stably
-//     on its remaining low bits by shared-memory counting passes (least
-//     significant window first, skipping windows in which no key differs),
-//     and its node ids are written to the final order buffer F.
+// (c) Small buckets are finished in registers.  In the paper the recursion
+//     runs every bucket down to M == 0 and merge() then appends the leaf
+//     buckets (Sec. "Implementation in C++", Sec. 5.1); the paper itself notes
+//     that MSD sorting spends too long on small chunks (Sec. "Differences
+//     between Pbit and other algorithms sorting with bit key").  Here one warp
+//     takes a bucket of at most kFinCap nodes, sorts it stably on its
+//     remaining low bits by counting passes in registers (least significant
+//     4-bit window first, skipping windows in which no key differs), and
+//     writes its node ids to the final order buffer F.  Warps never wait for
+//     each other, so a whole SM's worth of buckets is in flight at once.
 // (d) The relink concatenates the sorted fragments: next[s[i]] = s[i+1],
 //     next[s[n-1]] = -1, root = s[0] -- the effect of the merge() chain
 //     (Sec. 5.1) done for all nodes at once.  For doubly-linked pools the
-//     predecessor pointers are rebuilt in the same pass (Sec. "Double-linked
+//     predecessor pointers are rebuilt in the same step (Sec. "Double-linked
 //     lists sorting").
 #include "pbit_internal.cuh"
 
 namespace pbit {
 
-constexpr int kFTPB = 512;
-constexpr int kFItems = 8;
-constexpr int kFCap = kFTPB * kFItems;  // largest bucket the finish kernel sorts
+constexpr int kFinCap = 512;             // largest bucket a warp finishes
 constexpr int kFD = 4;
 constexpr int kFBins = 1 << kFD;
+constexpr int kFWarps = 4;               // warps per finish CTA
 
+// One warp per bucket.  The bucket lives in the warp's two shared-memory
+// buffers; every window is two sweeps over its 32-element groups: count the
+// digits (4 ballots per group), then rank each group again and scatter it to
+// the other buffer at its digit's offset.  Keeping the keys in shared memory
+// instead of registers leaves room for many warps per SM, which is what hides
+// the load latency of one small bucket after another.
 template <typename KeyT>
-constexpr int finish_smem() {
-    return kFCap * (int)sizeof(KeyT) + kFCap * 4;
-}
-
-template <typename KeyT>
-__global__ void __launch_bounds__(kFTPB, 2) k_finish(Ctx c) {
-    extern __shared__ __align__(16) unsigned char f_smem[];
-    KeyT *s_key = reinterpret_cast<KeyT *>(f_smem);
-    int32_t *s_idx = reinterpret_cast<int32_t *>(f_smem + kFCap * sizeof(KeyT));
-    __shared__ uint32_t s_w[kFTPB / 32][kFBins];
-    __shared__ uint32_t s_off[kFBins];
-    __shared__ unsigned long long s_and, s_or;
-    __shared__ int s_e;
+__global__ void __launch_bounds__(32 * kFWarps) k_finish(Ctx c) {
+    __shared__ __align__(16) KeyT s_key[kFWarps][2][kFinCap];
+    __shared__ int32_t s_idx[kFWarps][2][kFinCap];
     if (*(volatile int32_t *)c.status)
         return;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
     const int nfin = c.ctr->fin_count;
-    while (true) {
-        __syncthreads();
-        if (tid == 0) {
-            s_e = atomicAdd(&c.ctr->fin_ctr, 1);
-            s_and = ~0ull;
-            s_or = 0ull;
-        }
-        __syncthreads();
-        const int e = s_e;
-        if (e >= nfin)
-            break;
+    const int64_t gw = (int64_t)blockIdx.x * kFWarps + wid, nw = (int64_t)gridDim.x * kFWarps;
+    long long my_elems = 0;
+    for (int64_t e = gw; e < nfin; e += nw) {
         const Fin f = c.fin[e];
-        const int mode = f.mode_buf >> 8, buf = f.mode_buf & 1;
+        const int buf = f.mode_buf & 1;
         const int start = f.start, len = f.len;
-        const int32_t *src_idx = c.idxb[buf] + start;
-        int32_t *dst = c.F + start;
-        if (mode == 0 || len <= 1) {
-            if (tid == 0)
-                atomicAdd((unsigned long long *)&c.ctr->fin_copy_elems, (unsigned long long)len);
-            for (int j = tid; j < len; j += kFTPB)
-                dst[j] = src_idx[j];
-            continue;
-        }
-        if (tid == 0)
-            atomicAdd((unsigned long long *)&c.ctr->fin_sort_elems, (unsigned long long)len);
-        if (len > kFCap) {
+        if (len > kFinCap) {
             set_status(c.status, kStOverflow);
             continue;
         }
+        my_elems += len;
+        const int32_t *src_idx = c.idxb[buf] + start;
         const KeyT *src_key = reinterpret_cast<const KeyT *>(c.keyb[buf]) + start;
-        KeyT key[kFItems];
-        int32_t idx[kFItems];
+        int32_t *dst = c.F + start;
+        const int ng = (len + 31) >> 5;  // 32-element groups (warp-uniform)
+        int a = 0;                        // buffer holding the current order
         unsigned long long a_and = ~0ull, a_or = 0ull;
-        // item rounds of this warp that hold data (warp-uniform)
-        const int wbase = wid * (32 * kFItems);
-        const int nit = len <= wbase ? 0 : min(kFItems, (len - wbase + 31) / 32);
-#pragma unroll
-        for (int i = 0; i < kFItems; ++i) {
-            const int pos = wid * (32 * kFItems) + i * 32 + lane;
+        for (int g = 0; g < ng; ++g) {
+            const int pos = g * 32 + lane;
             if (pos < len) {
-                key[i] = src_key[pos];
-                idx[i] = src_idx[pos];
-                a_and &= (unsigned long long)key[i];
-                a_or |= (unsigned long long)key[i];
-            } else {
-                key[i] = 0;
-                idx[i] = 0;
+                const KeyT k = src_key[pos];
+                s_key[wid][0][pos] = k;
+                s_idx[wid][0][pos] = src_idx[pos];
+                a_and &= (unsigned long long)k;
+                a_or |= (unsigned long long)k;
             }
         }
 #pragma unroll
@@ -97,27 +71,51 @@ __global__ void __launch_bounds__(kFTPB, 2) k_finish(Ctx c) {
             a_and &= __shfl_xor_sync(kFull, a_and, o);
             a_or |= __shfl_xor_sync(kFull, a_or, o);
         }
-        if (lane == 0) {
-            atomicAnd(&s_and, a_and);
-            atomicOr(&s_or, a_or);
-        }
-        __syncthreads();
+        __syncwarp();
         const int hi = f.hi;
-        const unsigned long long vary = (s_and ^ s_or) & (hi >= 64 ? ~0ull : ((1ull << hi) - 1ull));
+        const unsigned long long vary = (a_and ^ a_or) & (hi >= 64 ? ~0ull : ((1ull << hi) - 1ull));
         for (int wl = 0; wl < hi; wl += kFD) {
             const int width = min(kFD, hi - wl);
             const unsigned dmask = (1u << width) - 1u;
             if (((vary >> wl) & dmask) == 0)
                 continue;  // every key agrees on this window
-            uint32_t rnk[kFItems];
-            uint32_t run = 0;
-#pragma unroll
-            for (int i = 0; i < kFItems; ++i) {
-                if (i >= nit)
-                    break;
-                const int pos = wid * (32 * kFItems) + i * 32 + lane;
+            const KeyT *ka = s_key[wid][a];
+            const int32_t *ia = s_idx[wid][a];
+            KeyT *kb = s_key[wid][a ^ 1];
+            int32_t *ib = s_idx[wid][a ^ 1];
+            // sweep 1: digit totals (lane d < 16 holds digit d)
+            uint32_t tot = 0;
+            for (int g = 0; g < ng; ++g) {
+                const int pos = g * 32 + lane;
                 const bool valid = pos < len;
-                const unsigned dig = valid ? (unsigned)((unsigned long long)key[i] >> wl) & dmask : 0u;
+                const unsigned dig = valid ? (unsigned)((unsigned long long)ka[pos] >> wl) & dmask : 0u;
+                unsigned mine = __ballot_sync(kFull, valid);
+#pragma unroll
+                for (int b = 0; b < kFD; ++b) {
+                    const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
+                    mine &= ((lane >> b) & 1) ? bb : ~bb;
+                }
+                tot += __popc(mine);
+            }
+            uint32_t incl = lane < kFBins ? tot : 0u;
+#pragma unroll
+            for (int o = 1; o < kFBins; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl += y;
+            }
+            uint32_t run = incl - (lane < kFBins ? tot : 0u);  // next free slot of digit lane
+            // sweep 2: stable scatter, group by group
+            for (int g = 0; g < ng; ++g) {
+                const int pos = g * 32 + lane;
+                const bool valid = pos < len;
+                KeyT k = 0;
+                int32_t x = 0;
+                if (valid) {
+                    k = ka[pos];
+                    x = ia[pos];
+                }
+                const unsigned dig = valid ? (unsigned)((unsigned long long)k >> wl) & dmask : 0u;
                 const unsigned vm = __ballot_sync(kFull, valid);
                 unsigned peers = vm, mine = vm;
 #pragma unroll
@@ -126,62 +124,27 @@ __global__ void __launch_bounds__(kFTPB, 2) k_finish(Ctx c) {
                     peers &= ((dig >> b) & 1u) ? bb : ~bb;
                     mine &= ((lane >> b) & 1) ? bb : ~bb;
                 }
-                rnk[i] = __shfl_sync(kFull, run, (int)dig) + __popc(peers & lt);
+                const uint32_t p = __shfl_sync(kFull, run, (int)dig) + __popc(peers & lt);
+                if (valid) {
+                    kb[p] = k;
+                    ib[p] = x;
+                }
                 run += __popc(mine);
             }
-            if (lane < kFBins)
-                s_w[wid][lane] = run;
-            __syncthreads();
-            if (wid == 0 && lane < kFBins) {
-                uint32_t tot = 0;
-#pragma unroll
-                for (int w = 0; w < kFTPB / 32; ++w) {
-                    const uint32_t x = s_w[w][lane];
-                    s_w[w][lane] = tot;
-                    tot += x;
-                }
-                uint32_t incl = tot;
-#pragma unroll
-                for (int o = 1; o < kFBins; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(0xffffu, incl, o);
-                    if (lane >= o)
-                        incl += y;
-                }
-                s_off[lane] = incl - tot;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < kFItems; ++i) {
-                if (i >= nit)
-                    break;
-                const int pos = wid * (32 * kFItems) + i * 32 + lane;
-                if (pos < len) {
-                    const unsigned dig = (unsigned)((unsigned long long)key[i] >> wl) & dmask;
-                    const uint32_t lp = s_off[dig] + s_w[wid][dig] + rnk[i];
-                    s_key[lp] = key[i];
-                    s_idx[lp] = idx[i];
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < kFItems; ++i) {
-                if (i >= nit)
-                    break;
-                const int pos = wid * (32 * kFItems) + i * 32 + lane;
-                if (pos < len) {
-                    key[i] = s_key[pos];
-                    idx[i] = s_idx[pos];
-                }
-            }
-            __syncthreads();
+            __syncwarp();
+            a ^= 1;
         }
-#pragma unroll
-        for (int i = 0; i < kFItems; ++i) {
-            const int pos = wid * (32 * kFItems) + i * 32 + lane;
+        const int32_t *ia = s_idx[wid][a];
+        for (int g = 0; g < ng; ++g) {
+            const int pos = g * 32 + lane;
             if (pos < len)
-                dst[pos] = idx[i];
+                dst[pos] = ia[pos];
         }
+        __syncwarp();
     }
+    // element count for the byte accounting (warp-uniform): one atomic per warp
+    if (lane == 0 && my_elems)
+        atomicAdd((unsigned long long *)&c.ctr->fin_sort_elems, (unsigned long long)my_elems);
 }
 
 // Stage (d): relink, direct form: one thread per sorted position writes
@@ -229,15 +192,62 @@ __global__ void k_relink(Ctx c) {
 // the node's pool block (2^rb nodes, a window of a few MB), then applied
 // block after block, so the stores of one window merge in L2 and leave as
 // full lines.  The two order buffers idxb[0], idxb[1] (free by now) hold the
-// pairs; bucket b owns slots [b << rb, (b << rb) + count).
+// pairs; bucket b owns slots [b << rb, (b << rb) + count).  Each tile first
+// groups its pairs by bucket in shared memory so that its writes to a
+// bucket are one contiguous run.
 constexpr int kRelTPB = 256;
 constexpr int kRelItems = 16;
 constexpr int kRelTile = kRelTPB * kRelItems;
 constexpr int kMaxRelBuckets = 512;
+constexpr int kCursorStride = 32;  // one 128-byte line per bucket cursor
+
+struct RelSmem {
+    int32_t cnt[kMaxRelBuckets];
+    int32_t loc[kMaxRelBuckets + 1];
+    int32_t base[kMaxRelBuckets];
+    int32_t sv[kRelTile];
+    int32_t ss[kRelTile];
+    uint16_t sb[kRelTile];
+};
+
+// Block-wide exclusive scan of one int per thread.
+__device__ int rel_excl_scan(int v, int *total, int *sh /* >= 33 ints */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = (lane < nw) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o)
+                s += y;
+        }
+        if (lane < nw)
+            sh[lane] = s;
+        if (lane == 31)
+            sh[32] = s;
+    }
+    __syncthreads();
+    const int base = (wid > 0) ? sh[wid - 1] : 0;
+    *total = sh[32];
+    const int r = base + x - v;
+    __syncthreads();
+    return r;
+}
 
 __global__ void __launch_bounds__(kRelTPB) k_relink_part(Ctx c, int rb) {
-    __shared__ int32_t s_cnt[kMaxRelBuckets];
-    __shared__ int32_t s_base[kMaxRelBuckets];
+    extern __shared__ __align__(16) unsigned char rel_smem[];
+    RelSmem &S = *reinterpret_cast<RelSmem *>(rel_smem);
+    __shared__ int sh[40];
     if (*(volatile int32_t *)c.status)
         return;
     const int32_t nv = c.ctr->n_virt;
@@ -247,22 +257,31 @@ __global__ void __launch_bounds__(kRelTPB) k_relink_part(Ctx c, int rb) {
     int32_t *tv = c.idxb[0], *ts = c.idxb[1];
     for (int64_t q0 = (int64_t)blockIdx.x * kRelTile; q0 < nv; q0 += (int64_t)gridDim.x * kRelTile) {
         for (int b = threadIdx.x; b < nb; b += kRelTPB)
-            s_cnt[b] = 0;
+            S.cnt[b] = 0;
         __syncthreads();
         int32_t vv[kRelItems], ss[kRelItems], rk[kRelItems];
+        // all loads first (independent, in flight together)
+        int32_t f0[kRelItems], f1[kRelItems];
+#pragma unroll
+        for (int i = 0; i < kRelItems; ++i) {
+            const int64_t q = q0 + i * kRelTPB + threadIdx.x;
+            f0[i] = q < nv ? c.F[q] : 0;
+            f1[i] = q + 1 < nv ? c.F[q + 1] : 0;
+        }
 #pragma unroll
         for (int i = 0; i < kRelItems; ++i) {
             const int64_t q = q0 + i * kRelTPB + threadIdx.x;
             vv[i] = -1;
+            ss[i] = -1;
             if (q < nv) {
-                const int lst = upper_index(c.out_base, L, (int32_t)q);
+                const int lst = L == 1 ? 0 : upper_index(c.out_base, L, (int32_t)q);
                 const ListDesc &d = c.desc[lst];
-                const int32_t loc = c.F[q] - d.out_base;
+                const int32_t loc = f0[i] - d.out_base;
                 const int64_t end = (int64_t)d.out_base + d.n;
                 int32_t succ = -1;
                 bool bad = loc < 0 || loc >= d.n;
                 if (q + 1 < end) {
-                    const int32_t ls = c.F[q + 1] - d.out_base;
+                    const int32_t ls = f1[i] - d.out_base;
                     bad |= ls < 0 || ls >= d.n;
                     succ = d.id_base + ls;
                     if (doubly && !bad)
@@ -278,36 +297,67 @@ __global__ void __launch_bounds__(kRelTPB) k_relink_part(Ctx c, int rb) {
                         if (doubly)
                             *(int32_t *)((unsigned char *)d.prev + (int64_t)vv[i] * d.prev_stride) = -1;
                     }
-                    rk[i] = atomicAdd(&s_cnt[vv[i] >> rb], 1);
                 }
             }
         }
+#pragma unroll
+        for (int i = 0; i < kRelItems; ++i)
+            rk[i] = vv[i] >= 0 ? atomicAdd(&S.cnt[vv[i] >> rb], 1) : 0;
         __syncthreads();
-        for (int b = threadIdx.x; b < nb; b += kRelTPB)
-            s_base[b] = s_cnt[b] ? atomicAdd(&c.rel_cursor[b], s_cnt[b]) : 0;
+        // local bucket offsets (exclusive scan of the counts) and the global
+        // reservation of each bucket's run
+        {
+            const int per = (nb + kRelTPB - 1) / kRelTPB;  // buckets per thread (<= 2)
+            int sum = 0;
+            for (int j = 0; j < per; ++j) {
+                const int b = threadIdx.x * per + j;
+                sum += b < nb ? S.cnt[b] : 0;
+            }
+            int tot;
+            int ex = rel_excl_scan(sum, &tot, sh);
+            for (int j = 0; j < per; ++j) {
+                const int b = threadIdx.x * per + j;
+                if (b < nb) {
+                    S.loc[b] = ex;
+                    ex += S.cnt[b];
+                    S.base[b] = S.cnt[b] ? atomicAdd(&c.rel_cursor[b * kCursorStride], S.cnt[b]) : 0;
+                }
+            }
+            if (threadIdx.x == 0)
+                S.loc[nb] = tot;
+        }
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < kRelItems; ++i) {
             if (vv[i] >= 0) {
                 const int b = vv[i] >> rb;
-                const int64_t slot = ((int64_t)b << rb) + s_base[b] + rk[i];
-                tv[slot] = vv[i];
-                ts[slot] = ss[i];
+                const int p = S.loc[b] + rk[i];
+                S.sv[p] = vv[i];
+                S.ss[p] = ss[i];
+                S.sb[p] = (uint16_t)b;
             }
+        }
+        __syncthreads();
+        const int total = S.loc[nb];
+        for (int j = threadIdx.x; j < total; j += kRelTPB) {
+            const int b = S.sb[j];
+            const int64_t slot = ((int64_t)b << rb) + S.base[b] + (j - S.loc[b]);
+            tv[slot] = S.sv[j];
+            ts[slot] = S.ss[j];
         }
         __syncthreads();
     }
 }
 
-// Apply the pairs of node blocks [b0, b0 + nbk): one launch per window so
-// the stores in flight stay inside a few MB of next[].
+// Apply the pairs of node block b0: one launch per window so the stores in
+// flight stay inside a few MB of next[].
 __global__ void k_relink_apply(Ctx c, int rb, int b0) {
     if (*(volatile int32_t *)c.status)
         return;
     const int32_t *tv = c.idxb[0], *ts = c.idxb[1];
     unsigned char *next = reinterpret_cast<unsigned char *>(c.desc[0].next);
     const int64_t stride = c.desc[0].next_stride;
-    const int32_t cnt = c.rel_cursor[b0];
+    const int32_t cnt = c.rel_cursor[b0 * kCursorStride];
     const int64_t base = (int64_t)b0 << rb;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
         *(int32_t *)(next + (int64_t)tv[base + i] * stride) = ts[base + i];
@@ -333,9 +383,9 @@ __global__ void k_check_done(Ctx c, int iters) {
 
 template <typename KeyT>
 static void launch_finish_t(const Ctx &c, cudaStream_t s, int sms) {
-    constexpr int smem = finish_smem<KeyT>();
-    cudaFuncSetAttribute(k_finish<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_finish<KeyT><<<(unsigned)(sms * 2), kFTPB, smem, s>>>(c);
+    const int smem = (int)(kFWarps * 2 * kFinCap * (sizeof(KeyT) + 4));
+    const int per_sm = max(1, min(16, (200 * 1024) / smem));
+    k_finish<KeyT><<<(unsigned)(sms * per_sm), 32 * kFWarps, 0, s>>>(c);
     prof_mark("finish", s);
 }
 
@@ -348,8 +398,10 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
     }
     if (relink_blocked(c)) {
         const int rb = relink_bucket_bits(c);
-        const int64_t pblocks = min((int64_t)sms * 8, max((int64_t)1, (c.ncap + kRelTile - 1) / kRelTile));
-        k_relink_part<<<(unsigned)pblocks, kRelTPB, 0, s>>>(c, rb);
+        const int64_t pblocks = min((int64_t)sms * 4, max((int64_t)1, (c.ncap + kRelTile - 1) / kRelTile));
+        const int smem = (int)sizeof(RelSmem);
+        cudaFuncSetAttribute(k_relink_part, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_relink_part<<<(unsigned)pblocks, kRelTPB, smem, s>>>(c, rb);
         const int64_t ablocks = min((int64_t)sms * 8, (int64_t)(((1ll << rb) + 255) / 256));
         const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
         for (int b = 0; b < nb; ++b)
@@ -368,7 +420,7 @@ void launch_check_done(const Ctx &c, int iters, cudaStream_t s) {
     prof_mark("plan", s);
 }
 
-int finish_capacity() { return kFCap; }
+int finish_capacity() { return kFinCap; }
 
 // Blocked relink when every list shares one pool (not the request server's
 // per-request pools): window of 2^rb nodes = at most 16 MB of next[].
@@ -379,6 +431,6 @@ int relink_bucket_bits(const Ctx &c) {
         ++rb;
     return rb;
 }
-int relink_max_buckets() { return kMaxRelBuckets; }
+int relink_max_buckets() { return kMaxRelBuckets * kCursorStride; }
 
 }  // namespace pbit

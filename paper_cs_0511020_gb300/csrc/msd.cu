@@ -202,7 +202,7 @@ template <typename KeyT>
 __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
     __shared__ uint32_t s_cnt[kBins];
     __shared__ unsigned long long s_and, s_or;
-    __shared__ int s_tile;
+    __shared__ int s_tile, s_aseg;
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1;
@@ -210,11 +210,13 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
     const int ntiles = c.ctr->stat_tiles[cur];
     const int rbase = c.ctr->brows[cur];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long my_elems = 0;
     if (threadIdx.x < kBins)
         s_cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         s_and = ~0ull;
         s_or = 0ull;
+        s_aseg = -1;
     }
     while (true) {
         __syncthreads();
@@ -225,6 +227,15 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         if (g >= ntiles)
             break;
         const int s = upper_index(c.pend_tile_base[cur], P, g);
+        if (threadIdx.x == 0 && s != s_aseg) {  // AND/OR are merged per segment, not per tile
+            if (s_aseg >= 0) {
+                atomicAnd(&c.pand[cur][s_aseg], s_and);
+                atomicOr(&c.por[cur][s_aseg], s_or);
+            }
+            s_and = ~0ull;
+            s_or = 0ull;
+            s_aseg = s;
+        }
         const Seg sg = c.pend[cur][s];
         const int k = g - c.pend_tile_base[cur][s];
         const int64_t b0 = (int64_t)sg.start + (int64_t)k * kTile;
@@ -232,8 +243,7 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         const KeyT *keys = reinterpret_cast<const KeyT *>(c.keyb[sg.buf & 1]);
         const int hi = sg.hi, lo = max(hi - kD, 0);
         const unsigned dmask = (1u << (hi - lo)) - 1u;
-        if (threadIdx.x == 0)
-            atomicAdd((unsigned long long *)&c.ctr->stat_elems[it], (unsigned long long)cnt);
+        my_elems += cnt;
         unsigned long long kv[kItems];
 #pragma unroll
         for (int u = 0; u < kItems; ++u) {
@@ -277,12 +287,14 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
                 c.tcnt[cur][row * kBins + threadIdx.x] = s_cnt[threadIdx.x];
             s_cnt[threadIdx.x] = 0;
         }
-        if (threadIdx.x == 0) {
-            atomicAnd(&c.pand[cur][s], s_and);
-            atomicOr(&c.por[cur][s], s_or);
-            s_and = ~0ull;
-            s_or = 0ull;
+    }
+    if (threadIdx.x == 0) {
+        if (s_aseg >= 0) {
+            atomicAnd(&c.pand[cur][s_aseg], s_and);
+            atomicOr(&c.por[cur][s_aseg], s_or);
         }
+        if (my_elems)
+            atomicAdd((unsigned long long *)&c.ctr->stat_elems[it], (unsigned long long)my_elems);
     }
 }
 
@@ -307,14 +319,14 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
     int fin_total = 0;
     for (int r0 = 0; r0 < P; r0 += blockDim.x) {
         const int s = r0 + threadIdx.x;
-        int kind = 0;  // 1 fin copy, 2 fin sort, 3 active, 4 pending again
+        int kind = 0;  // 1 small (no varying bit), 2 small, 3 active, 4 pending again, 5 active final
         Seg sg{0, 0, 0, 0, 0, 0, 0};
         int t = 0;
         if (s < P) {
             sg = c.pend[cur][s];
             const unsigned long long v = (c.por[cur][s] ^ c.pand[cur][s]) & low_mask(sg.hi);
             if (sg.len <= 1 || v == 0) {
-                kind = 1;
+                kind = sg.len <= c.cutoff ? 1 : 5;
             } else {
                 t = top_bit(v);
                 if (sg.len <= c.cutoff)
@@ -326,7 +338,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
         const int tiles = kind == 4 ? tiles_of(sg.len, kTile) : 0;
         int tf, ta, tr, tt;
         const int pf = block_excl_scan(kind == 1 || kind == 2, &tf, sh);
-        const int pa = block_excl_scan(kind == 3, &ta, sh);
+        const int pa = block_excl_scan(kind == 3 || kind == 5, &ta, sh);
         const int pr = block_excl_scan(kind == 4, &tr, sh);
         const int pt = block_excl_scan(tiles, &tt, sh);
         if (kind == 1 || kind == 2) {
@@ -335,11 +347,11 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
                 c.fin[k] = Fin{sg.start, sg.len, kind == 2 ? t + 1 : 0, ((kind == 2 ? 1 : 0) << 8) | (sg.buf & 1)};
             else
                 set_status(c.status, kStOverflow);
-        } else if (kind == 3) {
+        } else if (kind == 3 || kind == 5) {
             const int64_t a = (int64_t)s_act_base + pa;
             if (a < c.seg_cap)
                 c.act[cur][a] = Seg{sg.start, sg.len, (int16_t)max(sg.hi - kD, 0), sg.hi, sg.buf,
-                                    rbase + c.pend_tile_base[cur][s], 0};
+                                    rbase + c.pend_tile_base[cur][s], kind == 5 ? 1 : 0};
             else
                 set_status(c.status, kStOverflow);
         } else if (kind == 4) {
@@ -372,28 +384,36 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
     }
     __syncthreads();
     // tile, scan-chunk and next-row bases of all active segments of this pass
+    // (8 consecutive segments per thread per round)
+    constexpr int kPer = 8;
     const int A = (int)min((int64_t)s_act_base, c.seg_cap);
     long long my_elems = 0, my_final = 0;
-    for (int r0 = 0; r0 < A; r0 += blockDim.x) {
-        const int a = r0 + threadIdx.x;
+    for (int r0 = 0; r0 < A; r0 += blockDim.x * kPer) {
+        const int a0 = r0 + threadIdx.x * kPer;
         int tiles = 0, chunks = 0, nrows = 0;
-        if (a < A) {
-            const Seg sa = c.act[cur][a];
-            tiles = tiles_of(sa.len, kTile);
-            chunks = tiles_of(tiles, kScanRows);
-            nrows = sa.lo > 0 ? tiles + kRowPad : 0;
+        for (int u = 0; u < kPer && a0 + u < A; ++u) {
+            const Seg sa = c.act[cur][a0 + u];
+            const int nt = tiles_of(sa.len, kTile);
+            tiles += nt;
+            chunks += nt > 1 ? tiles_of(nt, kScanRows) : 0;
+            nrows += (sa.lo > 0 && !sa.final) ? nt + kRowPad : 0;
             my_elems += sa.len;
-            if (sa.lo == 0)
+            if (sa.lo == 0 || sa.final)
                 my_final += sa.len;
         }
         int tt, tc, tn;
-        const int pt = block_excl_scan(tiles, &tt, sh);
-        const int pc = block_excl_scan(chunks, &tc, sh);
-        const int pn = block_excl_scan(nrows, &tn, sh);
-        if (a < A) {
-            c.act_tile_base[cur][a] = s_tile_base + pt;
-            c.act_chunk_base[cur][a] = s_chunk_base + pc;
-            c.act_nrow_base[cur][a] = s_nrow_base + pn;
+        int pt = block_excl_scan(tiles, &tt, sh);
+        int pc = block_excl_scan(chunks, &tc, sh);
+        int pn = block_excl_scan(nrows, &tn, sh);
+        for (int u = 0; u < kPer && a0 + u < A; ++u) {
+            const Seg sa = c.act[cur][a0 + u];
+            const int nt = tiles_of(sa.len, kTile);
+            c.act_tile_base[cur][a0 + u] = s_tile_base + pt;
+            c.act_chunk_base[cur][a0 + u] = s_chunk_base + pc;
+            c.act_nrow_base[cur][a0 + u] = s_nrow_base + pn;
+            pt += nt;
+            pc += nt > 1 ? tiles_of(nt, kScanRows) : 0;
+            pn += (sa.lo > 0 && !sa.final) ? nt + kRowPad : 0;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -470,51 +490,34 @@ __global__ void __launch_bounds__(kTPB) k_tile_scan(Ctx c, int it) {
 }
 
 // ------------------------------------------------------------ chunk_scan
-// Per active segment: exclusive prefixes over its chunks (in place) and the
-// segment's digit histogram.
+// One warp per active segment (lanes 0..15 = digits): exclusive prefixes over
+// its chunks (in place) and the segment's digit histogram.  A segment of one
+// tile has no chunk: its histogram is its tile's row.
 __global__ void __launch_bounds__(kTPB) k_chunk_scan(Ctx c, int it) {
-    __shared__ uint32_t sh[(kTPB / 32 + 1) * kBins];
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1;
     const int A = c.ctr->act_count[cur];
-    for (int a = blockIdx.x; a < A; a += gridDim.x) {
-        const int c0 = c.act_chunk_base[cur][a], c1 = c.act_chunk_base[cur][a + 1];
-        uint32_t base[kBins];
-#pragma unroll
-        for (int j = 0; j < kBins; ++j)
-            base[j] = 0;
-        for (int b = c0; b < c1; b += kTPB) {
-            const int ch = b + threadIdx.x;
-            uint32_t v[kBins], tot[kBins];
-            uint4 *row = reinterpret_cast<uint4 *>(c.ctot + (int64_t)ch * kBins);
-            if (ch < c1) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 x = row[q];
-                    v[4 * q] = x.x;
-                    v[4 * q + 1] = x.y;
-                    v[4 * q + 2] = x.z;
-                    v[4 * q + 3] = x.w;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kBins; ++j)
-                    v[j] = 0;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < A; a += nw) {
+        if (lane >= kBins)
+            continue;
+        const int nt = c.act_tile_base[cur][a + 1] - c.act_tile_base[cur][a];
+        uint32_t run = 0;
+        if (nt == 1) {
+            run = c.tcnt[cur][(int64_t)c.act[cur][a].row * kBins + lane];
+        } else {
+            const int c0 = c.act_chunk_base[cur][a], c1 = c.act_chunk_base[cur][a + 1];
+            for (int ch = c0; ch < c1; ++ch) {
+                uint32_t *p = c.ctot + (int64_t)ch * kBins + lane;
+                const uint32_t t = *p;
+                *p = run;
+                run += t;
             }
-            block_excl_scan16(v, tot, sh);
-            if (ch < c1) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    row[q] = make_uint4(v[4 * q] + base[4 * q], v[4 * q + 1] + base[4 * q + 1],
-                                        v[4 * q + 2] + base[4 * q + 2], v[4 * q + 3] + base[4 * q + 3]);
-            }
-#pragma unroll
-            for (int j = 0; j < kBins; ++j)
-                base[j] += tot[j];
         }
-        if (threadIdx.x < kBins)
-            c.act_hist[cur][(int64_t)a * kBins + threadIdx.x] = base[threadIdx.x];
+        c.act_hist[cur][a * kBins + lane] = run;
     }
 }
 
@@ -528,6 +531,8 @@ struct PassSmem {
     int32_t nrow[kBins];              // first next-pass row of each output bucket
     int32_t k0[kBins];                // next-pass tile of this tile's first element per bucket
     uint32_t nc[kBins * 2 * kBins];   // counts per (bucket, next tile k0/k0+1, next digit)
+    unsigned long long aand[kBins], aor[kBins];  // AND/OR per bucket, merged over this CTA's tiles
+    int32_t aseg;                     // segment those belong to (-1: none)
     int32_t st_seg[2], st_cnt[2], st_k[2], st_shk[2], st_shi[2];
     int32_t nt[2];
     alignas(8) uint64_t bar[2];
@@ -603,6 +608,12 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
     }
     for (int i = tid; i < kBins * 2 * kBins; i += kTPB)
         S.nc[i] = 0;
+    if (tid < kBins) {
+        S.aand[tid] = ~0ull;
+        S.aor[tid] = 0ull;
+    }
+    if (tid == 0)
+        S.aseg = -1;
     uint32_t phase[2] = {0, 0};
     int st = 0;
     if (tid == 0) {
@@ -643,15 +654,31 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
             }
             ex -= h;
             nt_d -= (uint32_t)tiles_of(h, kTile);
-            const int ch = c.act_chunk_base[cur][s] + k / kScanRows;
-            const uint32_t before = c.ctot[(int64_t)ch * kBins + d] +
-                                    c.tcnt[cur][((int64_t)sg.row + k) * kBins + d];
+            uint32_t before = 0;  // the first tile of a segment starts every bucket
+            if (k > 0) {
+                const int ch = c.act_chunk_base[cur][s] + k / kScanRows;
+                before = c.ctot[(int64_t)ch * kBins + d] + c.tcnt[cur][((int64_t)sg.row + k) * kBins + d];
+            }
             S.bstart[d] = sg.start + (int32_t)ex;
             S.gbase[d] = sg.start + (int32_t)ex + (int32_t)before;
             S.k0[d] = (int32_t)(before >> kTileLog);
             S.nrow[d] = c.act_nrow_base[cur][s] + (int32_t)nt_d;
+            const int as = S.aseg;
+            if (as != s) {  // new segment: flush the merged AND/OR of the previous one
+                if (as >= 0 && (S.aand[d] != ~0ull || S.aor[d] != 0ull)) {
+                    atomicAnd(&c.band[cur][(int64_t)as * kBins + d], S.aand[d]);
+                    atomicOr(&c.bor[cur][(int64_t)as * kBins + d], S.aor[d]);
+                }
+                S.aand[d] = ~0ull;
+                S.aor[d] = 0ull;
+            }
+            __syncwarp(0xffffu);
+            if (d == 0)
+                S.aseg = s;
         }
-        const bool landed = mbar_wait_bounded(&S.bar[st], phase[st], 1ll << 26);
+        // one thread waits for the copy (acquire), the barrier then publishes
+        // the tile to the whole CTA
+        const bool landed = (tid != 0) || mbar_wait_bounded(&S.bar[st], phase[st], 1ll << 26);
         if (!__syncthreads_and(landed)) {
             set_status(c.status, PBIT_ETIMEOUT);
             if (tid == 0) {  // wait (bounded) for the copies still in flight before leaving
@@ -736,7 +763,7 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
         const int seg_end = sg.start + sg.len;
         KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(sg.buf & 1) ^ 1]);
         int32_t *oidx = c.idxb[(sg.buf & 1) ^ 1];
-        if (lo == 0) {
+        if (lo == 0 || sg.final) {
             for (int j = tid; j < cnt; j += kTPB) {
                 const unsigned dig = (unsigned)((unsigned long long)ok[j] >> lo) & dmask;
                 const int dst = S.gbase[dig] + (j - (int)S.tile_off[dig]);
@@ -780,9 +807,8 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                     oo |= __shfl_xor_sync(kFull, oo, o);
                 }
                 if (lane == 0) {
-                    const int64_t r = (int64_t)s * kBins + d;
-                    atomicAnd(&c.band[cur][r], aa);
-                    atomicOr(&c.bor[cur][r], oo);
+                    S.aand[d] &= aa;  // this warp alone owns digit d here
+                    S.aor[d] |= oo;
                 }
             }
             __syncthreads();
@@ -803,18 +829,23 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
         g = S.nt[st ^ 1];
         st ^= 1;
     }
+    if (tid < kBins && S.aseg >= 0 && (S.aand[tid] != ~0ull || S.aor[tid] != 0ull)) {
+        atomicAnd(&c.band[cur][(int64_t)S.aseg * kBins + tid], S.aand[tid]);
+        atomicOr(&c.bor[cur][(int64_t)S.aseg * kBins + tid], S.aor[tid]);
+    }
 }
 
 // ------------------------------------------------------------------ plan
-// kinds: 0 none, 1 fin copy, 2 fin sort, 3 next active, 4 pending
+// kinds: 0 none, 1 small (no varying bit), 2 small, 3 next active, 4 pending,
+// 5 next active final (all keys equal; written straight to F by the pass)
 __device__ __forceinline__ int classify_bucket(const Ctx &c, int cur, int s, const Seg &sg, int d,
                                                uint32_t cnt, int *t_out) {
-    if (cnt == 0 || sg.lo == 0)
+    if (cnt == 0 || sg.lo == 0 || sg.final)
         return 0;
     const int64_t r = (int64_t)s * kBins + d;
     const unsigned long long v = (c.bor[cur][r] ^ c.band[cur][r]) & low_mask(sg.lo);
     if (cnt == 1 || v == 0)
-        return 1;
+        return (int)cnt <= c.cutoff ? 1 : 5;
     const int t = top_bit(v);
     *t_out = t;
     if ((int)cnt <= c.cutoff)
@@ -837,7 +868,7 @@ __global__ void k_plan_count(Ctx c, int it) {
             int t = 0;
             const uint32_t cnt = h[d];
             const int kd = classify_bucket(c, cur, s, sg, d, cnt, &t);
-            na += kd == 3;
+            na += kd == 3 || kd == 5;
             np += kd == 4;
             nf += (kd == 1 || kd == 2);
             nt += (kd == 4) ? tiles_of(cnt, kTile) : 0;
@@ -861,16 +892,30 @@ __global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
         s_t = c.ctr->stat_tiles[nxt];
     }
     __syncthreads();
-    for (int r0 = 0; r0 < A; r0 += blockDim.x) {
-        const int s = r0 + threadIdx.x;
-        const int4 v = (s < A) ? c.plan_cnt[s] : make_int4(0, 0, 0, 0);
+    constexpr int kPer = 8;
+    for (int r0 = 0; r0 < A; r0 += blockDim.x * kPer) {
+        const int s0 = r0 + threadIdx.x * kPer;
+        int4 sum = make_int4(0, 0, 0, 0);
+        for (int u = 0; u < kPer && s0 + u < A; ++u) {
+            const int4 v = c.plan_cnt[s0 + u];
+            sum.x += v.x;
+            sum.y += v.y;
+            sum.z += v.z;
+            sum.w += v.w;
+        }
         int ta, tp, tf, tt;
-        const int pa = block_excl_scan(v.x, &ta, sh);
-        const int pp = block_excl_scan(v.y, &tp, sh);
-        const int pf = block_excl_scan(v.z, &tf, sh);
-        const int pt = block_excl_scan(v.w, &tt, sh);
-        if (s < A)
-            c.plan_cnt[s] = make_int4(s_a + pa, s_p + pp, s_f + pf, s_t + pt);
+        int pa = block_excl_scan(sum.x, &ta, sh);
+        int pp = block_excl_scan(sum.y, &tp, sh);
+        int pf = block_excl_scan(sum.z, &tf, sh);
+        int pt = block_excl_scan(sum.w, &tt, sh);
+        for (int u = 0; u < kPer && s0 + u < A; ++u) {
+            const int4 v = c.plan_cnt[s0 + u];
+            c.plan_cnt[s0 + u] = make_int4(s_a + pa, s_p + pp, s_f + pf, s_t + pt);
+            pa += v.x;
+            pp += v.y;
+            pf += v.z;
+            pt += v.w;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             s_a += ta;
@@ -913,10 +958,10 @@ __global__ void k_plan_write(Ctx c, int it) {
                     c.fin[f] = Fin{bstart, (int32_t)cnt, kd == 2 ? t + 1 : 0,
                                    ((kd == 2 ? 1 : 0) << 8) | ((sg.buf & 1) ^ 1)};
                 ++f;
-            } else if (kd == 3) {
+            } else if (kd == 3 || kd == 5) {
                 if (a < c.seg_cap)
                     c.act[nxt][a] = Seg{bstart, (int32_t)cnt, (int16_t)max(sg.lo - kD, 0), sg.lo,
-                                        (sg.buf & 1) ^ 1, nrow, 0};
+                                        (sg.buf & 1) ^ 1, nrow, kd == 5 ? 1 : 0};
                 ++a;
             } else if (kd == 4) {
                 if (p < c.seg_cap) {
@@ -944,7 +989,7 @@ static void launch_iter_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     k_plan_pending<<<1, 1024, 0, s>>>(c, it);
     prof_mark("plan", s);
     k_tile_scan<<<sms * 4, kTPB, 0, s>>>(c, it);
-    k_chunk_scan<<<sms * 2, kTPB, 0, s>>>(c, it);
+    k_chunk_scan<<<sms * 4, kTPB, 0, s>>>(c, it);
     prof_mark("scan", s);
     k_pass<KeyT><<<sms * per_sm, kTPB, smem, s>>>(c, it);
     prof_mark("pass", s);

@@ -41,12 +41,12 @@ struct Seg {
     int16_t hi;
     int32_t buf;
     int32_t row;  // first row of its per-tile digit counts (tcnt)
-    int32_t pad;
+    int32_t final;  // 1: keys are all equal; the pass writes it straight to F
 };
 
-// A finished-or-small run: mode 0 = copy the node ids to the final buffer,
-// mode 1 = sort on bits [0, hi) in shared memory first.  buf = order buffer
-// parity that holds it.
+// A small run (at most the finish capacity): sorted on bits [0, hi) by one
+// warp and written to the final buffer.  buf = order buffer parity that
+// holds it (low bit of mode_buf).
 struct Fin {
     int32_t start;
     int32_t len;
@@ -56,17 +56,23 @@ struct Fin {
 
 constexpr int kMaxIters = 64;
 
+// Work counters that many CTAs hit at once sit on their own 128-byte lines
+// (an atomic on a line is serialized in one L2 slice).
+struct alignas(128) HotCounter {
+    int32_t v;
+    int32_t pad[31];
+};
+
 struct Counters {
+    HotCounter chunk_next;     // bump allocator of ranking chunks
+    HotCounter task_next;      // work counter of the ranking walk
+    HotCounter fin_ctr;        // work counter of the finish kernel
     int32_t n_virt;            // total nodes over all lists
-    int32_t chunk_next;        // bump allocator of ranking chunks
     int32_t fin_count;
-    int32_t fin_ctr;           // work counter of the finish kernel
     int32_t act_count[2];
     int32_t pend_count[2];
     int32_t num_tiles[2];
     int32_t stat_tiles[2];
-    int32_t task_next;         // work counter of the ranking walk
-    int32_t pad0;
     int32_t brows[2];          // tcnt rows handed to the previous pass's buckets
     int32_t num_chunks[2];     // scan chunks of the pass
     // element counts for the per-kernel algorithmic-byte accounting

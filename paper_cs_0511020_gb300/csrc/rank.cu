@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256, 6) k_walk(Ctx c) {
         if (im != 0 && q_next >= q_end && !exhausted) {
             int32_t base = 0;
             if (lane == 0)
-                base = atomicAdd(&c.ctr->task_next, kTaskBatch);
+                base = atomicAdd(&c.ctr->task_next.v, kTaskBatch);
             base = __shfl_sync(kFull, base, 0);
             if (base >= ntask) {
                 exhausted = true;
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256, 6) k_walk(Ctx c) {
             if (avail < cnt) {
                 int32_t base = 0;
                 if (lane == 0)
-                    base = atomicAdd(&c.ctr->chunk_next, kSuper);
+                    base = atomicAdd(&c.ctr->chunk_next.v, kSuper);
                 base = __shfl_sync(kFull, base, 0);
                 if (need && r >= avail)
                     chunk = base + (r - avail);
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256) k_emit(Ctx c, int fin) {
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t nchunks = min((int64_t)c.ctr->chunk_next, c.chunk_cap);
+    const int64_t nchunks = min((int64_t)c.ctr->chunk_next.v, c.chunk_cap);
     const int64_t *w = c.wy[fin];
     const KeyT *ckey = reinterpret_cast<const KeyT *>(c.chunk_key);
     KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[0]);

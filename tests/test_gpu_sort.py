@@ -235,8 +235,8 @@ def test_tune_variants(pb):
     n = 400000
     nxt, root = I.random_list(n, 151)
     key = I.uniform_keys(n, 4, 152)
-    for tune in ({"smem_cutoff": 1024}, {"ruler_stride": 8}, {"ruler_stride": 256},
-                 {"smem_cutoff": 256, "ruler_stride": 64}):
+    for tune in ({"smem_cutoff": 64}, {"ruler_stride": 8}, {"ruler_stride": 256},
+                 {"smem_cutoff": 256, "ruler_stride": 64}, {"smem_cutoff": 1}):
         _check_vs_oracle(pb, nxt, key, root, 32, tune=tune)
 
 
