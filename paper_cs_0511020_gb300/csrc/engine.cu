@@ -165,7 +165,7 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms) 
     zero(x.ctr, 0, sizeof(Counters));
     x.status = (int32_t *)take(64);
     zero(x.status, 0, 64);
-    x.new_roots = (int32_t *)take(64);  // single-list result slot
+    x.new_roots = (int32_t *)take(4 * (size_t)(z.L > 16 ? z.L : 16));  // list heads (single/served calls)
     x.desc = (ListDesc *)take(sizeof(ListDesc) * (size_t)z.L);
     x.out_base = (int32_t *)take(4 * (size_t)(z.L + 1));
     x.root_task = (int32_t *)take(4 * (size_t)z.L);
@@ -275,8 +275,8 @@ pbit_status map_status(int st) {
     return PBIT_ECUDA;
 }
 
-static bool check_pool(const pbit_pool *p, int M, int K) {
-    if (!p || !p->next || !p->key)
+bool check_pool(const pbit_pool *p, int M, int K) {
+    if (!p || (p->pool_size > 0 && (!p->next || !p->key)))  // an empty pool may have no storage
         return false;
     const int kb = p->key_type;
     if (kb != 1 && kb != 2 && kb != 4 && kb != 8)
@@ -293,7 +293,8 @@ static bool check_pool(const pbit_pool *p, int M, int K) {
         return false;
     if ((p->flags & PBIT_FLOAT) && kb < 4)
         return false;
-    if ((p->flags & PBIT_DOUBLY) && (!p->prev || p->prev_stride_bytes < 4 || p->prev_stride_bytes % 4 != 0))
+    if ((p->flags & PBIT_DOUBLY) && ((p->pool_size > 0 && !p->prev) || p->prev_stride_bytes < 4 ||
+                                     p->prev_stride_bytes % 4 != 0))
         return false;
     if (p->flags & ~(PBIT_SIGNED | PBIT_DESCENDING | PBIT_DOUBLY | PBIT_FLOAT))
         return false;
@@ -302,7 +303,7 @@ static bool check_pool(const pbit_pool *p, int M, int K) {
     return true;
 }
 
-static ListDesc pool_template(const pbit_pool *p) {
+ListDesc pool_template(const pbit_pool *p) {
     ListDesc t{};
     t.next = p->next;
     t.key = (const unsigned char *)p->key;

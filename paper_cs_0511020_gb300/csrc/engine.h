@@ -36,5 +36,7 @@ pbit_status enqueue_sort(const Ctx &c, const std::vector<Memset> &ms, int mode, 
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s, int sms,
                          int64_t *launches);
 pbit_status map_status(int st);
+bool check_pool(const pbit_pool *p, int M, int K);
+ListDesc pool_template(const pbit_pool *p);
 
 }  // namespace pbit

@@ -1,0 +1,352 @@
+// serve.cu -- request server: continuous batching of sort requests.
+//
+// Callers submit lists that live in their own device pools.  A scheduler
+// thread admits queued requests into batches that fit a slot of the device
+// arena (the memory budget split over the server's CUDA streams), so a batch
+// formed from requests that arrived while other batches run on the GPU is
+// launched as soon as a slot frees up, and up to `streams` batches overlap on
+// the device.  A batch is one sort call whose lists are its requests (each
+// list with its own pool, relinked in place); requests of one batch share
+// key type, flags and M.  If a batch fails (a malformed list), its requests
+// are retried one by one so each gets its own status.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "engine.h"
+
+namespace pbit {
+
+struct SrvReq {
+    uint64_t ticket;
+    pbit_pool pool;
+    int32_t root;
+    int64_t n;
+    int M, K;
+    bool solo = false;      // retry alone (its batch failed)
+    int status = PBIT_EPENDING;
+    int32_t new_root = -1;
+};
+
+struct SrvSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    ListDesc *h_desc = nullptr;  // pinned, max_batch entries
+    int32_t *h_out = nullptr;    // pinned: status, then one head per list
+    std::vector<SrvReq *> reqs;
+    bool busy = false;
+};
+
+static bool compatible(const SrvReq *a, const SrvReq *b) {
+    return a->pool.key_type == b->pool.key_type && a->pool.flags == b->pool.flags && a->M == b->M && !a->solo &&
+           !b->solo;
+}
+
+static size_t batch_ws(int64_t nodes, int32_t lists, int kb) {
+    size_t w = 0;
+    if (pbit_workspace_size(nodes, lists, kb, nullptr, &w) != PBIT_OK)
+        return (size_t)-1;
+    return w;
+}
+
+}  // namespace pbit
+
+using namespace pbit;
+
+struct pbit_server {
+    int device = 0;
+    int max_batch = 64;
+    unsigned char *arena = nullptr;
+    std::vector<SrvSlot> slots;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<SrvReq *> queue;
+    std::unordered_map<uint64_t, SrvReq *> reqs;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    std::thread worker;
+    int64_t submitted = 0, completed = 0, batches = 0, max_in_batch = 0, peak_bytes = 0, in_flight_bytes = 0;
+};
+
+namespace pbit {
+
+// Take a batch for a slot from the queue (lock held).
+static std::vector<SrvReq *> take_batch(pbit_server *s, const SrvSlot &slot, int64_t *nodes_out) {
+    std::vector<SrvReq *> b;
+    if (s->queue.empty())
+        return b;
+    SrvReq *first = s->queue.front();
+    int64_t nodes = first->n;
+    if (batch_ws(nodes, 1, first->pool.key_type) > slot.ws_bytes)
+        return b;  // waits for a slot that is large enough (all slots are equal: never)
+    b.push_back(first);
+    s->queue.pop_front();
+    if (!first->solo) {
+        const size_t window = 256;  // how far down the queue to look for companions
+        for (size_t i = 0; i < s->queue.size() && i < window && (int)b.size() < s->max_batch;) {
+            SrvReq *r = s->queue[i];
+            if (compatible(first, r) && batch_ws(nodes + r->n, (int32_t)b.size() + 1, r->pool.key_type) <= slot.ws_bytes) {
+                b.push_back(r);
+                nodes += r->n;
+                s->queue.erase(s->queue.begin() + (ptrdiff_t)i);
+            } else {
+                ++i;
+            }
+        }
+    }
+    *nodes_out = nodes;
+    return b;
+}
+
+static pbit_status launch_batch(SrvSlot &slot, const std::vector<SrvReq *> &b, int64_t nodes) {
+    const SrvReq *r0 = b[0];
+    const int L = (int)b.size();
+    int32_t ob = 0;
+    for (int i = 0; i < L; ++i) {
+        ListDesc d = pool_template(&b[i]->pool);
+        d.n = (int32_t)b[i]->n;
+        d.root = b[i]->root;
+        d.id_base = 0;
+        d.out_base = ob;
+        ob += d.n;
+        slot.h_desc[i] = d;
+    }
+    Tune t;
+    resolve_tune(nullptr, nodes, r0->pool.key_type, &t);
+    const int sms = device_sms();
+    Sizes z = compute_sizes(nodes, L, r0->pool.key_type, t, sms);
+    Ctx c;
+    std::vector<Memset> ms;
+    if (bind(z, slot.ws, &c, &ms) > slot.ws_bytes)
+        return PBIT_ENOMEM;
+    c.flags = r0->pool.flags;
+    c.shared_pool = 0;
+    c.desc_next_stride = 4;
+    if (cudaMemcpyAsync(c.desc, slot.h_desc, sizeof(ListDesc) * (size_t)L, cudaMemcpyHostToDevice, slot.stream) !=
+        cudaSuccess)
+        return PBIT_ECUDA;
+    pbit_status rc = enqueue_sort(c, ms, 1, nullptr, nullptr, nullptr, r0->M, slot.stream, sms, nullptr);
+    if (rc != PBIT_OK)
+        return rc;
+    if (cudaMemcpyAsync(slot.h_out, c.status, 4, cudaMemcpyDeviceToHost, slot.stream) != cudaSuccess ||
+        cudaMemcpyAsync(slot.h_out + 1, c.new_roots, 4 * (size_t)L, cudaMemcpyDeviceToHost, slot.stream) !=
+            cudaSuccess ||
+        cudaEventRecord(slot.ev, slot.stream) != cudaSuccess)
+        return PBIT_ECUDA;
+    return PBIT_OK;
+}
+
+static void serve_loop(pbit_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        bool progress = false;
+        // completions
+        for (SrvSlot &slot : s->slots) {
+            if (!slot.busy || cudaEventQuery(slot.ev) != cudaSuccess)
+                continue;
+            const pbit_status st = map_status(slot.h_out[0]);
+            if (st == PBIT_OK || slot.reqs.size() == 1) {
+                for (size_t i = 0; i < slot.reqs.size(); ++i) {
+                    SrvReq *r = slot.reqs[i];
+                    r->status = st;
+                    r->new_root = st == PBIT_OK ? slot.h_out[1 + i] : -1;
+                    ++s->completed;
+                }
+            } else {  // isolate the failing request(s): retry each alone, in order
+                for (size_t i = slot.reqs.size(); i-- > 0;) {
+                    slot.reqs[i]->solo = true;
+                    s->queue.push_front(slot.reqs[i]);
+                }
+            }
+            s->in_flight_bytes -= (int64_t)slot.ws_bytes;
+            slot.reqs.clear();
+            slot.busy = false;
+            progress = true;
+            s->cv_done.notify_all();
+        }
+        // admissions
+        for (SrvSlot &slot : s->slots) {
+            if (slot.busy || s->queue.empty())
+                continue;
+            int64_t nodes = 0;
+            std::vector<SrvReq *> b = take_batch(s, slot, &nodes);
+            if (b.empty())
+                break;
+            slot.busy = true;  // owned by this thread while the lock is released
+            lk.unlock();       // launching takes a while: let submitters in
+            const pbit_status rc = launch_batch(slot, b, nodes);
+            lk.lock();
+            slot.busy = false;
+            if (rc != PBIT_OK) {
+                for (SrvReq *r : b) {
+                    r->status = rc;
+                    ++s->completed;
+                }
+                s->cv_done.notify_all();
+                continue;
+            }
+            slot.reqs = b;
+            slot.busy = true;
+            ++s->batches;
+            s->max_in_batch = std::max<int64_t>(s->max_in_batch, (int64_t)b.size());
+            s->in_flight_bytes += (int64_t)slot.ws_bytes;
+            s->peak_bytes = std::max(s->peak_bytes, s->in_flight_bytes);
+            progress = true;
+        }
+        if (!progress) {
+            bool any_busy = false;
+            for (const SrvSlot &slot : s->slots)
+                any_busy |= slot.busy;
+            // idle: sleep until a submit; busy: poll the events again shortly
+            s->cv_work.wait_for(lk, any_busy ? std::chrono::microseconds(20) : std::chrono::milliseconds(50));
+        }
+    }
+}
+
+}  // namespace pbit
+
+extern "C" {
+
+pbit_status pbit_serve_create(pbit_server **out, size_t mem_budget_bytes, int32_t device, int32_t streams,
+                              int32_t max_batch) {
+    if (!out || streams < 1 || streams > 16 || max_batch < 1 || mem_budget_bytes < (1u << 20))
+        return PBIT_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return PBIT_ECUDA;
+    pbit_server *s = new pbit_server();
+    s->device = device;
+    s->max_batch = max_batch;
+    const size_t per = (mem_budget_bytes / (size_t)streams) & ~(size_t)255;
+    if (cudaMalloc((void **)&s->arena, per * (size_t)streams) != cudaSuccess) {
+        delete s;
+        return PBIT_ENOMEM;
+    }
+    s->slots.resize((size_t)streams);
+    for (int i = 0; i < streams; ++i) {
+        SrvSlot &sl = s->slots[(size_t)i];
+        sl.ws = s->arena + per * (size_t)i;
+        sl.ws_bytes = per;
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost((void **)&sl.h_desc, sizeof(ListDesc) * (size_t)max_batch) != cudaSuccess ||
+            cudaMallocHost((void **)&sl.h_out, 4 * (size_t)(max_batch + 1)) != cudaSuccess) {
+            pbit_serve_destroy(s);
+            return PBIT_ECUDA;
+        }
+    }
+    s->worker = std::thread(serve_loop, s);
+    *out = s;
+    return PBIT_OK;
+}
+
+pbit_status pbit_serve_submit(pbit_server *s, const pbit_pool *pool, int32_t root, int64_t n, int32_t M, int32_t K,
+                              uint64_t *ticket) {
+    if (!s || !pool || !ticket || !check_pool(pool, M, K) || n != pool->pool_size)
+        return PBIT_EINVAL;
+    if (n > 0 && (root < 0 || root >= n))
+        return PBIT_EBADLIST;
+    if (n == 0 && root != -1)
+        return PBIT_EBADLIST;
+    if (n > 0 && batch_ws(n, 1, pool->key_type) > s->slots[0].ws_bytes)
+        return PBIT_EAGAIN;  // can never fit the budget
+    SrvReq *r = new SrvReq();
+    r->pool = *pool;
+    r->root = root;
+    r->n = n;
+    r->M = M;
+    r->K = K;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        r->ticket = s->next_ticket++;
+        s->reqs[r->ticket] = r;
+        ++s->submitted;
+        if (n == 0) {  // an empty list is done at once (the paper returns NULL)
+            r->status = PBIT_OK;
+            r->new_root = -1;
+            ++s->completed;
+        } else {
+            s->queue.push_back(r);
+        }
+    }
+    s->cv_work.notify_one();
+    *ticket = r->ticket;
+    return PBIT_OK;
+}
+
+pbit_status pbit_serve_poll(pbit_server *s, uint64_t ticket, int32_t *new_root) {
+    if (!s)
+        return PBIT_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+        return PBIT_EINVAL;
+    const SrvReq *r = it->second;
+    if (r->status == PBIT_OK && new_root)
+        *new_root = r->new_root;
+    return (pbit_status)r->status;
+}
+
+pbit_status pbit_serve_wait(pbit_server *s, uint64_t ticket, int32_t *new_root, int64_t timeout_ms) {
+    if (!s)
+        return PBIT_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+        return PBIT_EINVAL;
+    const SrvReq *r = it->second;
+    s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                        [&] { return r->status != PBIT_EPENDING; });
+    if (r->status == PBIT_OK && new_root)
+        *new_root = r->new_root;
+    return (pbit_status)r->status;
+}
+
+void pbit_serve_stats(pbit_server *s, int64_t *out5) {
+    if (!s || !out5)
+        return;
+    std::lock_guard<std::mutex> g(s->mu);
+    out5[0] = s->submitted;
+    out5[1] = s->completed;
+    out5[2] = s->batches;
+    out5[3] = s->max_in_batch;
+    out5[4] = s->peak_bytes;
+}
+
+void pbit_serve_destroy(pbit_server *s) {
+    if (!s)
+        return;
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable())
+        s->worker.join();
+    for (SrvSlot &sl : s->slots) {
+        if (sl.stream)
+            cudaStreamSynchronize(sl.stream);
+        if (sl.ev)
+            cudaEventDestroy(sl.ev);
+        if (sl.stream)
+            cudaStreamDestroy(sl.stream);
+        if (sl.h_desc)
+            cudaFreeHost(sl.h_desc);
+        if (sl.h_out)
+            cudaFreeHost(sl.h_out);
+    }
+    if (s->arena)
+        cudaFree(s->arena);
+    for (auto &kv : s->reqs)
+        delete kv.second;
+    delete s;
+}
+
+}  // extern "C"

@@ -78,6 +78,18 @@ def lib():
         L.pbit_profile_enable.argtypes = [i32]
         L.pbit_profile_read.restype = i32
         L.pbit_profile_read.argtypes = [vp, i32]
+        L.pbit_serve_create.restype = ctypes.c_int
+        L.pbit_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, i32, i32, i32]
+        L.pbit_serve_submit.restype = ctypes.c_int
+        L.pbit_serve_submit.argtypes = [vp, vp, i32, i64, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
+        L.pbit_serve_poll.restype = ctypes.c_int
+        L.pbit_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32)]
+        L.pbit_serve_wait.restype = ctypes.c_int
+        L.pbit_serve_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32), i64]
+        L.pbit_serve_stats.restype = None
+        L.pbit_serve_stats.argtypes = [vp, ctypes.POINTER(i64)]
+        L.pbit_serve_destroy.restype = None
+        L.pbit_serve_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -232,3 +244,54 @@ def sort_pool_list_host(pool: Pool, root: int, n: int, M: int, K: int = 4, ws=No
     if check and st != OK:
         raise PbitError(st, "pbit_sort_list_host")
     return st, int(nr.value)
+
+
+class Server:
+    """Request server (pbit_serve_*): continuous batching of sort requests
+    whose pools the caller keeps alive until they finish."""
+
+    def __init__(self, mem_budget_bytes: int = 16 << 30, device: int = 0, streams: int = 4,
+                 max_batch: int = 64):
+        self._h = ctypes.c_void_p()
+        st = lib().pbit_serve_create(ctypes.byref(self._h), int(mem_budget_bytes), int(device), int(streams),
+                                     int(max_batch))
+        if st != OK:
+            raise PbitError(st, "pbit_serve_create")
+        self._keep = {}
+
+    def submit(self, pool: Pool, root: int, n: int, M: int, K: int = 4, keep=None) -> int:
+        """Queue one request; returns its ticket (raises on refusal)."""
+        t = ctypes.c_uint64(0)
+        st = lib().pbit_serve_submit(self._h, ctypes.addressof(pool), int(root), int(n), int(M), int(K),
+                                     ctypes.byref(t))
+        if st != OK:
+            raise PbitError(st, "pbit_serve_submit")
+        self._keep[t.value] = (pool, keep)
+        return int(t.value)
+
+    def poll(self, ticket: int):
+        nr = ctypes.c_int32(-7)
+        st = lib().pbit_serve_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(nr))
+        return st, int(nr.value)
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        nr = ctypes.c_int32(-7)
+        st = lib().pbit_serve_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(nr), int(timeout_ms))
+        return st, int(nr.value)
+
+    def stats(self) -> dict:
+        a = (ctypes.c_int64 * 5)()
+        lib().pbit_serve_stats(self._h, a)
+        return dict(submitted=a[0], completed=a[1], batches=a[2], max_batch=a[3], peak_bytes=a[4])
+
+    def close(self):
+        if self._h:
+            lib().pbit_serve_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
