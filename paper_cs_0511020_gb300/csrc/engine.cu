@@ -8,6 +8,7 @@
 // pool size, the number of lists, the key width and the tune; no call
 // allocates device memory.
 #include <cstdio>
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -123,7 +124,10 @@ Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms) {
     const int64_t S = 1ll << t.log2S;
     z.R0 = (ncap + S - 1) / S;
     z.Rcap = z.R0 + L;
-    const int64_t walk_warps = (int64_t)sms * 8 * 8;
+    // slack: every walk warp may hold one partly used super-chunk of 64 chunks
+    // (grid as launch_walk sizes it)
+    const int64_t walk_blocks = std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, ((z.Rcap + 31) / 32 + 7) / 8));
+    const int64_t walk_warps = walk_blocks * 8;
     z.chunk_cap = (ncap + z.CH - 1) / z.CH + z.Rcap + 64 * walk_warps + 64;
     z.seg_cap = ncap / (t.cutoff + 1) + 2;
     const int64_t iters = (8 * kb + t.digit_bits - 1) / t.digit_bits;
@@ -133,7 +137,7 @@ Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms) {
 }
 
 // Carve the workspace.  With ws == nullptr only the size is computed.
-size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms) {
+size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> unsigned char * {
         unsigned char *p = ws ? ws + off : nullptr;
@@ -141,8 +145,8 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms) 
         return p;
     };
     auto zero = [&](void *p, int v, size_t bytes) {
-        if (ms && p)
-            ms->push_back(Memset{p, v, bytes});
+        if (ms && p && !ms->push(Memset{p, v, bytes}))
+            ms->count = -1;  // capacity exceeded: enqueue_sort refuses
     };
     Ctx x;
     std::memset(&x, 0, sizeof x);
@@ -226,12 +230,15 @@ static int ceil_log2(int64_t x) {
 }
 
 // Enqueue the whole sort on stream s.  Returns PBIT_ECUDA if a launch failed.
-pbit_status enqueue_sort(const Ctx &c, const std::vector<Memset> &ms, int mode, const ListDesc *tmpl,
+pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const ListDesc *tmpl,
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s,
                          int sms, int64_t *launches) {
     int64_t n = 0;  // kernel launches
     prof_begin(s);
-    for (const Memset &m : ms) {
+    if (ms.count < 0)
+        return PBIT_ENOMEM;
+    for (int i = 0; i < ms.count; ++i) {
+        const Memset &m = ms.items[i];
         if (cudaMemsetAsync(m.p, m.v, m.bytes, s) != cudaSuccess)
             return PBIT_ECUDA;
     }
@@ -325,7 +332,7 @@ static pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const 
     const int sms = device_sms();
     Sizes z = compute_sizes(pool->pool_size, num_lists, pool->key_type, t, sms);
     Ctx c;
-    std::vector<Memset> ms;
+    MemsetList ms;
     const size_t need = bind(z, (unsigned char *)ws, &c, &ms);
     if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255))
         return ws_bytes < need ? PBIT_ENOMEM : PBIT_EINVAL;

@@ -28,11 +28,25 @@ struct Memset {
     size_t bytes;
 };
 
+// The memsets a sort call issues before its kernels (fixed capacity: a call
+// makes no host allocation).
+struct MemsetList {
+    static constexpr int kCap = 48;
+    Memset items[kCap];
+    int count = 0;
+    bool push(const Memset &m) {
+        if (count == kCap)
+            return false;
+        items[count++] = m;
+        return true;
+    }
+};
+
 int device_sms();
 bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out);
 Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms);
-size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, std::vector<Memset> *ms);
-pbit_status enqueue_sort(const Ctx &c, const std::vector<Memset> &ms, int mode, const ListDesc *tmpl,
+size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms);
+pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const ListDesc *tmpl,
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s, int sms,
                          int64_t *launches);
 pbit_status map_status(int st);

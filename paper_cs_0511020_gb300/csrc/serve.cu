@@ -123,7 +123,7 @@ static pbit_status launch_batch(SrvSlot &slot, const std::vector<SrvReq *> &b, i
     const int sms = device_sms();
     Sizes z = compute_sizes(nodes, L, r0->pool.key_type, t, sms);
     Ctx c;
-    std::vector<Memset> ms;
+    MemsetList ms;
     if (bind(z, slot.ws, &c, &ms) > slot.ws_bytes)
         return PBIT_ENOMEM;
     c.flags = r0->pool.flags;
