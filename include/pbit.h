@@ -132,6 +132,30 @@ pbit_status pbit_sort_list_host(const pbit_pool *host_pool, int32_t root, int64_
                                 void *stream);
 
 /*
+ * pbit_sort_list without a workspace, for callers that cannot allocate device
+ * memory (a process whose allocator has given all device memory to a
+ * framework's pool, a loop where an allocation and the synchronization it
+ * implies cannot be afforded, a wrapper whose API has no room for a
+ * workspace).  The paper has no counterpart: this is a library convenience.
+ *   - The scratch space is a fixed 8 MiB array in the library's device
+ *     image; every GPU that loads the library holds it until the process
+ *     exits.  Lists longer than 65536 nodes are rejected with PBIT_ENOMEM.
+ *   - The call allocates nothing: no device memory, no pinned host memory,
+ *     no CUDA event or stream (per-kernel profiling is suspended for it).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on that device.
+ *   - All calls share the one array, which keeps the last call's contents;
+ *     each call clears what it needs cleared.  Calls whose GPU work overlaps
+ *     (other threads, other streams) race on the array: serialize them.
+ * Same arguments, validation and result as pbit_sort_list (device pool,
+ * pool_size == n, next[] relinked in place, *new_root_host on PBIT_OK);
+ * synchronizes `stream`.
+ */
+pbit_status pbit_sort_list_noalloc(const pbit_pool *pool, int32_t root, int64_t n, int32_t M, int32_t K,
+                                   int32_t *new_root_host, void *stream);
+
+/*
  * Number of kernel launches the last sort call on this thread enqueued (for
  * benchmarks that report launches; 0 before any call).
  */

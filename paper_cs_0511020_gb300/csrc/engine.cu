@@ -56,6 +56,12 @@ void prof_mark(const char *name, cudaStream_t s) {
         g_prof.marks.emplace_back(name, e);
 }
 
+bool prof_set(bool on) {
+    const bool was = g_prof.on;
+    g_prof.on = on;
+    return was;
+}
+
 static void prof_begin(cudaStream_t s) {
     if (!g_prof.on)
         return;

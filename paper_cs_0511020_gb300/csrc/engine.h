@@ -51,6 +51,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
                          int64_t *launches);
 pbit_status map_status(int st);
 bool check_pool(const pbit_pool *p, int M, int K);
+bool prof_set(bool on);  // per-thread event profiling on/off; returns the previous state
 ListDesc pool_template(const pbit_pool *p);
 
 }  // namespace pbit

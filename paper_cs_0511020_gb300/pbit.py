@@ -18,7 +18,7 @@ OK, EINVAL, ENOMEM, EBADLIST, ETIMEOUT, ECUDA, EAGAIN, EPENDING = range(8)
 SIGNED, DESCENDING, DOUBLY, FLOAT = 1, 2, 4, 8
 
 EXPORTS = ("pbit_status_string", "pbit_workspace_size", "pbit_sort_list", "pbit_sort_lists_batched",
-           "pbit_workspace_size_host", "pbit_sort_list_host", "pbit_last_launch_count",
+           "pbit_workspace_size_host", "pbit_sort_list_host", "pbit_sort_list_noalloc", "pbit_last_launch_count",
            "pbit_profile_enable", "pbit_profile_read", "pbit_serve_create", "pbit_serve_submit",
            "pbit_serve_poll", "pbit_serve_wait", "pbit_serve_stats", "pbit_serve_destroy")
 
@@ -74,6 +74,8 @@ def lib():
         L.pbit_sort_list_host.restype = ctypes.c_int
         L.pbit_sort_list_host.argtypes = [vp, i32, i64, i32, i32, ctypes.POINTER(i32), vp, vp,
                                           ctypes.c_size_t, vp]
+        L.pbit_sort_list_noalloc.restype = ctypes.c_int
+        L.pbit_sort_list_noalloc.argtypes = [vp, i32, i64, i32, i32, ctypes.POINTER(i32), vp]
         L.pbit_profile_enable.restype = None
         L.pbit_profile_enable.argtypes = [i32]
         L.pbit_profile_read.restype = i32
@@ -196,6 +198,22 @@ def sort_lists_batched(next_t, key_t, roots_t, offsets_t, M=None, K=4, flags=0, 
     pool = make_pool(next_t, key_t, flags)
     M = 8 * key_t.element_size() if M is None else M
     return sort_pool_batched(pool, roots_t, offsets_t, M, K, None, ws, tune, stream)[1]
+
+
+NOALLOC_MAX_NODES = 1 << 16
+
+
+def sort_pool_list_noalloc(pool: Pool, root: int, n: int, M: int, K: int = 4, stream=None, check: bool = True):
+    """pbit_sort_list_noalloc: same as sort_pool_list but with the library's
+    static scratch array instead of a workspace (lists up to
+    NOALLOC_MAX_NODES nodes; for callers that cannot allocate device
+    memory).  Returns (status, new_root)."""
+    nr = ctypes.c_int32(-7)
+    st = lib().pbit_sort_list_noalloc(ctypes.addressof(pool), int(root), int(n), int(M), int(K), ctypes.byref(nr),
+                                      _stream_handle(stream))
+    if check and st != OK:
+        raise PbitError(st, "pbit_sort_list_noalloc")
+    return st, int(nr.value)
 
 
 def last_launch_count() -> int:
