@@ -89,18 +89,29 @@ def batched_pool(lengths: np.ndarray, key_bytes: int, seed: int):
     np.cumsum(lengths, out=off[1:])
     total = int(off[-1])
     g = rng(seed)
-    # one random permutation per list, built from a global random key sort
-    # inside each range (vectorised: sort (list id, random) pairs)
-    r = g.random(total)
-    lid = np.repeat(np.arange(lengths.size, dtype=np.int64), lengths)
-    perm = np.lexsort((r, lid)).astype(np.int64)      # positions grouped by list, random inside
     nxt = np.full(total, -1, dtype=np.int32)
-    # within list i, perm[off[i]:off[i+1]] is a random order of its pool range
-    has_succ = np.ones(total, dtype=bool)
-    has_succ[off[1:][lengths > 0] - 1] = False
-    src = perm[has_succ]
-    dst = np.roll(perm, -1)[has_succ]
-    nxt[src] = dst.astype(np.int32)
-    roots = np.where(lengths > 0, perm[np.minimum(off[:-1], max(total - 1, 0))], -1).astype(np.int32)
+    roots = np.full(lengths.size, -1, dtype=np.int32)
+    for i, ln in enumerate(lengths):
+        if ln == 0:
+            continue
+        a = int(off[i])
+        order = g.permutation(int(ln)).astype(np.int32) + np.int32(a)
+        nxt[order[:-1]] = order[1:]
+        roots[i] = order[0]
     key = uniform_keys(total, key_bytes, seed + 1)
     return nxt, key, roots, off
+
+
+def config4_lengths(seed: int, count: int = 4096) -> np.ndarray:
+    """Batched workload: `count` list lengths log-uniform in [16, 2^20]."""
+    return log_uniform_lengths(count, 4.0, 20.0, seed, 16, 1 << 20)
+
+
+def config5_requests(count: int, seed: int):
+    """Request stream: exponential gaps of mean 0.5 ms (Poisson, 2000/s),
+    lengths log-uniform in [2^4, 2^24], key widths 2:4:8 in 1:2:1."""
+    g = rng(seed)
+    gaps = g.exponential(0.5e-3, count)
+    lengths = np.clip(np.floor(2.0 ** (4.0 + 20.0 * g.random(count))), 16, 1 << 24).astype(np.int64)
+    kb = g.choice(np.array([2, 4, 4, 8]), size=count)
+    return np.cumsum(gaps), lengths, kb
