@@ -41,6 +41,11 @@ def parse():
     ap.add_argument("--log2n", type=int, default=27, help="list size (27 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2n", type=int, default=24)
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4096-list batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the request-serving leg")
+    ap.add_argument("--batched-lists", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=2000, help="timed requests of the serving leg")
+    ap.add_argument("--serve-warmup", type=int, default=200)
     return ap.parse_args()
 
 
@@ -269,6 +274,12 @@ def run_ours(a):
         cpu = {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the oracle (single-threaded literal Pbit) on one 2^{a.cpu_sample_log2n}-node list "
                          f"of the same recipe ({dt:.1f} s)"}
+    del d_next0, d_next, d_key, ws_h, h_next0, h_next, h_key
+    torch.cuda.empty_cache()
+    batched = None if (a.no_batched or world > 1) else run_batched(a, torch, pbit, I)
+    torch.cuda.empty_cache()
+    serve = None if (a.no_serve or world > 1) else run_serve(a, torch, pbit, I)
+    torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -283,12 +294,158 @@ def run_ours(a):
         "roofline": roof,
         "kernels": per_kernel,
         "cpu_baseline": cpu,
+        "batched": batched,
+        "serve": serve,
         "clocks": clocks,
         "wall_s": wall,
     }
     print(json.dumps(line))
     if world > 1:
         tdist.destroy_process_group()
+
+
+def run_batched(a, torch, pbit, I):
+    """Batched workload: 4096 lists in one pool, lengths log-uniform in
+    [16, 2^20], uint32 keys, random order per list, M=32.  The batch is
+    autotuned, captured once as a CUDA graph and replayed; the same lists are
+    then sorted one pbit_sort_list call at a time (the plain per-list path)."""
+    gen = torch.Generator(device="cuda").manual_seed(I.SEED_BASE + 4)
+    lens = I.config4_lengths(I.SEED_BASE + 4, a.batched_lists)
+    d_next0, d_key, d_roots, d_off = I.device_batched_pool(lens, 4, gen)
+    total = int(lens.sum())
+    d_next = d_next0.clone()
+    pool = pbit.make_pool(d_next, d_key)
+    best, tune_ms = pbit.autotune_batched(pool, d_roots, d_off, 32, 4, reps=2)
+    g = pbit.Graph.batched(pool, d_roots, d_off, 32, 4)
+    stream = torch.cuda.current_stream()
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    for _ in range(a.warmup):
+        d_next.copy_(d_next0)
+        g.launch(stream)
+        g.result(stream)
+    for i in range(a.steps):
+        d_next.copy_(d_next0)
+        e0[i].record(stream)
+        g.launch(stream)
+        e1[i].record(stream)
+        g.result(stream)  # status of this replay (synchronizes)
+    graph_ms = [e0[i].elapsed_time(e1[i]) for i in range(a.steps)]
+    gm = statistics.median(graph_ms)
+
+    # the plain per-list path: one synchronous pbit_sort_list per list, in
+    # order, each on its own slice of the pool with list-local indices
+    off = d_off.cpu().numpy()
+    lid = torch.repeat_interleave(torch.arange(lens.size, device="cuda"), torch.as_tensor(lens, device="cuda"))
+    base = d_off[:-1][lid].to(torch.int32)
+    loc0 = torch.where(d_next0 >= 0, d_next0 - base, d_next0)
+    loc = loc0.clone()
+    roots_loc = (d_roots - d_off[:-1].to(torch.int32)).cpu().numpy()
+    ws = pbit.alloc_workspace(pbit.workspace_size(int(lens.max()), 1, 4))
+    pools = [pbit.Pool(loc.data_ptr() + 4 * int(off[i]), 4, d_key.data_ptr() + 4 * int(off[i]), 4, 4, 0,
+                       int(lens[i]), 0, 0) for i in range(lens.size)]
+    fifo_s = []
+    for rep in range(2):
+        loc.copy_(loc0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(lens.size):
+            st, _ = pbit.sort_pool_list(pools[i], int(roots_loc[i]), int(lens[i]), 32, 4, ws=ws, stream=stream,
+                                        check=False)
+            if st != pbit.OK:
+                raise pbit.PbitError(st, "per-list sort")
+        torch.cuda.synchronize()
+        fifo_s.append(time.perf_counter() - t0)
+    # both paths give the same next[] (list-local vs pool indices)
+    same = bool(torch.equal(torch.where(loc >= 0, loc + base, loc), d_next))
+    fm = min(fifo_s)
+    out = {"workload": f"{lens.size} lists in one SoA pool, lengths log-uniform in [16, 2^20] (seeded), "
+                       "uint32 keys uniform, random order per list, M=32, K=4",
+           "nodes": total, "lists": int(lens.size),
+           "graph": {"value": total / (gm / 1e3), "unit": UNIT, "ms_per_step": gm, "steps": a.steps,
+                     "graph_nodes": g.node_count(),
+                     "timing": "CUDA events around each graph replay; next[] restored before, outside them"},
+           "per_list": {"value": total / fm, "unit": UNIT, "ms": 1e3 * fm,
+                        "timing": "host wall clock over the whole loop of synchronous pbit_sort_list calls, "
+                                  "best of 2"},
+           "speedup_vs_per_list": fm * 1e3 / gm, "same_result": same,
+           "autotuned": {**best, "median_ms": tune_ms}}
+    g.close()
+    return out
+
+
+def run_serve(a, torch, pbit, I):
+    """Serving workload: open-loop Poisson arrivals (mean gap 0.5 ms), lengths
+    log-uniform in [2^4, 2^24], key widths 2/4/8 bytes in 1:2:1 (M = 8 x
+    width), pools resident on the device, 16 GB admission budget.  Latency =
+    completion seen by the scheduler - scheduled arrival (host monotonic
+    clock).  The same trace is then served FIFO, one synchronous
+    pbit_sort_list call at a time."""
+    R = a.serve_warmup + a.serve_requests
+    arr, lens, kbs = I.config5_requests(R, I.SEED_BASE + 5)  # arrival times (s), lengths, key widths
+    gen = torch.Generator(device="cuda").manual_seed(I.SEED_BASE + 5)
+    reqs = []
+    for i in range(R):
+        n, kb = int(lens[i]), int(kbs[i])
+        nxt, root = I.device_random_list(n, gen)
+        key = I.device_keys(n, kb, gen)
+        reqs.append([nxt, nxt.clone(), key, root, n, kb, pbit.make_pool(nxt, key)])
+    torch.cuda.synchronize()
+
+    def summarize(lat_ns, t_first, t_last, count_from):
+        lat = np.array(lat_ns[count_from:], dtype=np.float64) / 1e6
+        nodes = int(sum(int(lens[i]) for i in range(count_from, R)))
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "value": nodes / ((t_last - t_first) / 1e9), "unit": UNIT}
+
+    srv = pbit.Server(mem_budget_bytes=16 << 30, streams=4, max_batch=64)
+    tickets = []
+    t0 = time.monotonic_ns() + 20_000_000
+    sched = [t0 + int(x * 1e9) for x in arr]
+    for i, r in enumerate(reqs):
+        while time.monotonic_ns() < sched[i]:
+            pass
+        tickets.append(srv.submit(r[6], r[3], r[4], 8 * r[5], 4))
+    done = []
+    for i, t in enumerate(tickets):
+        st, _ = srv.wait(t, 600000)
+        if st != pbit.OK:
+            raise pbit.PbitError(st, "served request")
+        done.append(srv.times(t)[1])
+    stats = srv.stats()
+    srv.close()
+    W = a.serve_warmup
+    lat = [done[i] - sched[i] for i in range(R)]
+    served = summarize(lat, sched[W], max(done[W:]), W)
+
+    # the same trace served FIFO by the plain per-list call
+    for r in reqs:
+        r[0].copy_(r[1])
+    ws = pbit.alloc_workspace(max(pbit.workspace_size(1 << 24, 1, kb) for kb in (2, 4, 8)))
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.monotonic_ns() + 20_000_000
+    sched = [t0 + int(x * 1e9) for x in arr]
+    fdone = []
+    for i, r in enumerate(reqs):
+        while time.monotonic_ns() < sched[i]:
+            pass
+        st, _ = pbit.sort_pool_list(r[6], r[3], r[4], 8 * r[5], 4, ws=ws, stream=stream, check=False)
+        if st != pbit.OK:
+            raise pbit.PbitError(st, "FIFO request")
+        fdone.append(time.monotonic_ns())
+    flat = [fdone[i] - sched[i] for i in range(R)]
+    fifo = summarize(flat, sched[W], max(fdone[W:]), W)
+    offered = float(lens[W:].sum() / (arr[-1] - arr[W]))
+    return {"workload": "open-loop Poisson arrivals, mean gap 0.5 ms; lengths log-uniform in [2^4, 2^24]; "
+                        "uint16/uint32/uint64 keys 1:2:1, M = 8 x width; random order; uniform keys; "
+                        "16 GB admission budget, 4 streams, batches of up to 64",
+            "requests": a.serve_requests, "warmup_requests": W, "offered_nodes_per_s": offered,
+            "served": {**served, "batches": stats["batches"], "max_batch": stats["max_batch"],
+                       "peak_admitted_bytes": stats["peak_bytes"]},
+            "fifo_per_list": fifo,
+            "latency": "completion seen by the scheduler (served) or after the synchronous call returns "
+                       "(FIFO) minus the scheduled arrival, host monotonic clock"}
 
 
 def traffic_for(name, alg_bytes, log2n):

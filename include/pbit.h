@@ -75,10 +75,12 @@ typedef struct {
 
 /* Tuning knobs; any field <= 0 takes the built-in / autotuned default. */
 typedef struct {
-    int32_t digit_bits;   /* GPU digit width per MSD pass: 4 (16 buckets) or 8   */
+    int32_t digit_bits;   /* GPU digit width per MSD pass: 4 (16 buckets) only   */
     int32_t smem_cutoff;  /* buckets <= this many nodes are finished in smem     */
     int32_t ruler_stride; /* list ranking: one ruler per this many nodes (2^k)   */
-    int32_t reserved;
+    int32_t gather_pack;  /* 0: by size, 1: off, 2: on -- pack {next, key} per   */
+                          /* node before the ranking walk (one random access     */
+                          /* per hop instead of two)                             */
 } pbit_tune;
 
 /* Human-readable name of a status code (static string). */
@@ -179,6 +181,59 @@ typedef struct {
 void pbit_profile_enable(int32_t on);
 int32_t pbit_profile_read(pbit_kernel_stat *out, int32_t max);
 
+/* ------------------------------------------------------------ CUDA graphs
+ * A sort call captured once as a CUDA graph and replayed.  The launch
+ * sequence of a sort depends only on pool_size, num_lists, the key type, M
+ * and the tune, never on the data: every replay re-reads next[], key[],
+ * d_roots and d_offsets, so one graph sorts any lists laid out in the same
+ * pool (different list orders, keys, or list lengths in d_offsets).  The
+ * graph keeps the pointers it was created with: the pool, d_roots, d_offsets,
+ * d_new_roots and the workspace must stay allocated, at the same addresses,
+ * until pbit_graph_destroy.  Creating a graph enqueues no GPU work (the
+ * capture runs on a private stream); the graph belongs to the device current
+ * at creation.  Replays on one graph share its workspace: do not let two of
+ * them overlap.
+ */
+typedef struct pbit_graph pbit_graph;
+/* Capture pbit_sort_lists_batched(pool, num_lists, d_roots, d_offsets, M, K,
+ * d_new_roots, tune, ws, ws_bytes) (same arguments and contract). */
+pbit_status pbit_graph_create_batched(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
+                                      const int64_t *d_offsets, int32_t M, int32_t K, int32_t *d_new_roots,
+                                      const pbit_tune *tune, void *ws, size_t ws_bytes, pbit_graph **out);
+/* Capture pbit_sort_list(pool, root, n, M, K, ...): root and n are fixed in
+ * the graph; the new root is returned by pbit_graph_result. */
+pbit_status pbit_graph_create_single(const pbit_pool *pool, int32_t root, int64_t n, int32_t M, int32_t K,
+                                     const pbit_tune *tune, void *ws, size_t ws_bytes, pbit_graph **out);
+/* Enqueue one replay on `stream` (asynchronous: no status read-back). */
+pbit_status pbit_graph_launch(pbit_graph *g, void *stream);
+/* Synchronize `stream` and return the status of the last replay enqueued on
+ * it before this call; a single-list graph also writes *new_root_host. */
+pbit_status pbit_graph_result(pbit_graph *g, void *stream, int32_t *new_root_host);
+/* Number of nodes (memsets and kernels) in the graph. */
+int64_t pbit_graph_node_count(const pbit_graph *g);
+void pbit_graph_destroy(pbit_graph *g);
+
+/* --------------------------------------------------------------- autotuner
+ * Times the sort of the caller's batch under each candidate tune
+ * (shared-memory cutoff 128/256/512 x ruler stride 16/32/64/128; `reps`
+ * timed runs each after one warm-up, median kept) and returns the fastest in
+ * *best (and its median time in *best_ms).  Candidates whose workspace
+ * exceeds ws_bytes are skipped; pbit_autotune_workspace_size gives room for
+ * all of them.  The pool is restored to its input state before every trial
+ * and at the end (a temporary device copy of next[] / prev[] is allocated
+ * for the call), so on return the lists are NOT sorted.  The choice is
+ * remembered for this device, key type and size class (ceil log2 of
+ * pool_size and of num_lists): later calls with tune == NULL on a pool of
+ * that class take it whenever their workspace is large enough for it
+ * (pbit_workspace_size with tune == NULL then returns room for it).  If the
+ * environment variable PBIT_TUNE_FILE names a file, choices are appended to
+ * it and read back from it by later processes.  Synchronizes `stream`.
+ */
+pbit_status pbit_autotune_workspace_size(int64_t pool_size, int32_t num_lists, int32_t key_type, size_t *bytes);
+pbit_status pbit_autotune_batched(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
+                                  const int64_t *d_offsets, int32_t M, int32_t K, int32_t *d_new_roots, void *ws,
+                                  size_t ws_bytes, int32_t reps, void *stream, pbit_tune *best, float *best_ms);
+
 /* ------------------------------------------------------------------ serving
  * A server owns a device arena of at most mem_budget_bytes on `device` and a
  * scheduler thread.  Requests are admitted while the workspace bytes of all
@@ -203,6 +258,13 @@ pbit_status pbit_serve_poll(pbit_server *s, uint64_t ticket, int32_t *new_root);
 /* Block until the ticket finishes (or timeout_ms elapses: PBIT_EPENDING). */
 pbit_status pbit_serve_wait(pbit_server *s, uint64_t ticket, int32_t *new_root,
                             int64_t timeout_ms);
+/* Host steady-clock times (ns) of a ticket's submission and of the moment
+ * the scheduler saw it finish (0 while pending).  PBIT_EINVAL for an
+ * unknown ticket. */
+pbit_status pbit_serve_times(pbit_server *s, uint64_t ticket, int64_t *submit_ns, int64_t *done_ns);
+/* Forget a finished ticket (its record is freed; polling it then returns
+ * PBIT_EINVAL).  PBIT_EPENDING if it has not finished. */
+pbit_status pbit_serve_release(pbit_server *s, uint64_t ticket);
 /* Server counters: [0] submitted, [1] completed, [2] batches launched,
  * [3] max requests in one batch, [4] peak admitted bytes. */
 void pbit_serve_stats(pbit_server *s, int64_t *out5);

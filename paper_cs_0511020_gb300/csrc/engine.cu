@@ -35,6 +35,7 @@ struct ProfState {
     int64_t n = 0, rcap = 0, rounds = 0;
     int kb = 4;
     bool blocked_relink = false;
+    bool pack = false;
 };
 static thread_local ProfState g_prof;
 
@@ -97,6 +98,7 @@ bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out) {
     r.digit_bits = digit_bits();
     r.cutoff = finish_capacity();
     r.log2S = 5;
+    r.pack = 0;
     if (t) {
         if (t->digit_bits > 0 && t->digit_bits != digit_bits())
             return false;
@@ -113,6 +115,9 @@ bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out) {
                 return false;
             r.log2S = l;
         }
+        if (t->gather_pack < 0 || t->gather_pack > 2)
+            return false;
+        r.pack = t->gather_pack;
     }
     (void)pool_size;
     (void)kb;
@@ -139,6 +144,9 @@ Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms) {
     const int64_t iters = (8 * kb + t.digit_bits - 1) / t.digit_bits;
     z.fin_cap = L + (int64_t)(1 << t.digit_bits) * iters * z.seg_cap + 16;
     z.tile_cap = ncap / pass_tile() + z.seg_cap + 2;
+    // A random gather costs a whole DRAM sector or more: the pack turns the
+    // walk's two gathers per hop into one.
+    z.pack = t.pack == 2 || (t.pack == 0 && ncap * (4 + kb) > kPackAutoBytes);
     return z;
 }
 
@@ -191,11 +199,14 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     x.chunk_j0 = (int32_t *)take(4 * (size_t)z.chunk_cap);
     x.chunk_data = (int32_t *)take(4 * (size_t)z.chunk_cap * z.CH);
     x.chunk_key = take((size_t)z.kb * z.chunk_cap * z.CH);
-    for (int b = 0; b < 2; ++b)
+    // keyb[1], idxb[1] and F are adjacent: the ranking's pack array spans
+    // them (n * (kb + 8) bytes >= n * 8, and >= n * 16 when kb == 8)
+    for (int b = 0; b < 2; ++b) {
         x.keyb[b] = take((size_t)z.ncap * z.kb + 64);
-    for (int b = 0; b < 2; ++b)
         x.idxb[b] = (int32_t *)take((size_t)z.ncap * 4 + 64);
+    }
     x.F = (int32_t *)take((size_t)z.ncap * 4 + 64);
+    x.pack = z.pack ? x.keyb[1] : nullptr;
     x.row_cap = 2 * (z.ncap / pass_tile()) + 18 * z.seg_cap + 64;
     x.scan_cap = z.ncap / ((int64_t)pass_tile() * scan_rows()) + z.seg_cap + 2;
     for (int b = 0; b < 2; ++b) {
@@ -252,6 +263,9 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     Ctx cc = c;
     cc.M = M;
     launch_setup(cc, d_offsets, d_roots, mode, tmpl, s, sms);
+    launch_pack(cc, s, sms);
+    if (cc.pack)
+        ++n;
     launch_walk(cc, s, sms);
     const int rounds = ceil_log2(cc.Rcap) + 1;
     launch_wyllie(cc, s, sms, rounds);
@@ -270,6 +284,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
         g_prof.rounds = rounds;
         g_prof.kb = cc.key_bytes;
         g_prof.blocked_relink = relink_blocked(cc);
+        g_prof.pack = cc.pack != nullptr;
     }
     if (launches)
         *launches = n;
@@ -328,7 +343,7 @@ ListDesc pool_template(const pbit_pool *p) {
 }
 
 // Enqueue a sort of a pool with list ranges (d_offsets) or of one list.
-static pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
+pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
                                 const int64_t *d_offsets, int single_root, int64_t single_n, int M,
                                 int32_t *d_new_roots, const pbit_tune *tune, void *ws, size_t ws_bytes,
                                 cudaStream_t s, Ctx *out) {
@@ -337,6 +352,16 @@ static pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const 
         return PBIT_EINVAL;
     const int sms = device_sms();
     Sizes z = compute_sizes(pool->pool_size, num_lists, pool->key_type, t, sms);
+    pbit_tune cached;
+    if (!tune && tune_cache_lookup(pool->pool_size, num_lists, pool->key_type, &cached)) {
+        // the autotuned choice for this size class, when it fits the workspace
+        Tune tc;
+        if (resolve_tune(&cached, pool->pool_size, pool->key_type, &tc)) {
+            const Sizes zc = compute_sizes(pool->pool_size, num_lists, pool->key_type, tc, sms);
+            if (bind(zc, nullptr, nullptr, nullptr) <= ws_bytes)
+                z = zc;
+        }
+    }
     Ctx c;
     MemsetList ms;
     const size_t need = bind(z, (unsigned char *)ws, &c, &ms);
@@ -345,6 +370,9 @@ static pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const 
     c.flags = pool->flags;
     c.shared_pool = 1;
     c.desc_next_stride = pool->next_stride_bytes;
+    if (z.tune.pack == 0 && pool->key_type == 4 && pool->next_stride_bytes == 8 && pool->key_stride_bytes == 8 &&
+        (const unsigned char *)pool->key == (const unsigned char *)pool->next + 4)
+        c.pack = nullptr;  // {int32 next; uint32 key} nodes are packed already
     if (d_new_roots)
         c.new_roots = d_new_roots;
     ListDesc tmpl = pool_template(pool);
@@ -399,15 +427,7 @@ static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int
     return finish_call(c, host_root, s);
 }
 
-// Byte ranges of a pool: the next[] region, and the key[] / prev[] regions
-// when they do not lie inside it (AoS keeps the key inside the node).
-struct PoolSpan {
-    size_t next_bytes, key_bytes, prev_bytes;
-    bool key_inside;
-    ptrdiff_t key_off;
-};
-
-static PoolSpan pool_span(const pbit_pool *p) {
+PoolSpan pool_span(const pbit_pool *p) {
     PoolSpan r{};
     const int64_t n = p->pool_size;
     r.next_bytes = (size_t)(n > 0 ? (n - 1) * p->next_stride_bytes + 4 : 0);
@@ -453,8 +473,14 @@ pbit_status pbit_workspace_size(int64_t pool_size, int32_t num_lists, int32_t ke
     Tune t;
     if (!resolve_tune(tune, pool_size, key_type, &t))
         return PBIT_EINVAL;
-    Sizes z = compute_sizes(pool_size, num_lists, key_type, t, device_sms());
-    *bytes = bind(z, nullptr, nullptr, nullptr);
+    const int sms = device_sms();
+    size_t w = bind(compute_sizes(pool_size, num_lists, key_type, t, sms), nullptr, nullptr, nullptr);
+    pbit_tune cached;
+    Tune tc;
+    if (!tune && tune_cache_lookup(pool_size, num_lists, key_type, &cached) &&
+        resolve_tune(&cached, pool_size, key_type, &tc))  // room for either choice
+        w = std::max(w, bind(compute_sizes(pool_size, num_lists, key_type, tc, sms), nullptr, nullptr, nullptr));
+    *bytes = w;
     return PBIT_OK;
 }
 
@@ -519,7 +545,12 @@ int32_t pbit_profile_read(pbit_kernel_stat *out, int32_t max) {
         for (int32_t i = 0; i < cnt; ++i) {
             const char *nm = out[i].name;
             double b = 0;
-            if (!std::strcmp(nm, "walk") || !std::strcmp(nm, "emit")) {
+            const double rec = kb == 8 ? 16.0 : 8.0;  // packed record
+            if (!std::strcmp(nm, "pack")) {
+                b = n * (4.0 + kb + rec);
+            } else if (!std::strcmp(nm, "walk")) {
+                b = n * ((g_prof.pack ? rec : 4.0 + kb) + 4.0 + kb);
+            } else if (!std::strcmp(nm, "emit")) {
                 b = n * 2.0 * (4.0 + kb);
             } else if (!std::strcmp(nm, "wyllie")) {
                 b = (double)g_prof.rcap * (16.0 + 24.0 * (double)g_prof.rounds);

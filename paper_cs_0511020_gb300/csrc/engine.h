@@ -7,10 +7,16 @@
 
 namespace pbit {
 
+// Pools larger than this (next + key bytes) are packed before the walk
+// (measured: the pack pays for itself from about 2^18 nodes on, even while
+// the pool fits in L2).
+constexpr int64_t kPackAutoBytes = 2ll << 20;
+
 struct Tune {
     int digit_bits;
     int cutoff;
     int log2S;
+    int pack;  // 0 = by size, 1 = off, 2 = on (see Ctx::pack)
 };
 
 struct Sizes {
@@ -20,6 +26,7 @@ struct Sizes {
     Tune tune;
     int CH;
     int64_t R0, Rcap, chunk_cap, seg_cap, fin_cap, tile_cap;
+    bool pack;
 };
 
 struct Memset {
@@ -53,5 +60,26 @@ pbit_status map_status(int st);
 bool check_pool(const pbit_pool *p, int M, int K);
 bool prof_set(bool on);  // per-thread event profiling on/off; returns the previous state
 ListDesc pool_template(const pbit_pool *p);
+
+// Enqueue a sort of a pool with list ranges (d_offsets) or of one list
+// (d_offsets == nullptr: single_root, single_n); no synchronization.
+pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
+                         const int64_t *d_offsets, int single_root, int64_t single_n, int M,
+                         int32_t *d_new_roots, const pbit_tune *tune, void *ws, size_t ws_bytes,
+                         cudaStream_t s, Ctx *out);
+
+// Byte ranges of a pool: the next[] region, and the key[] / prev[] regions
+// when they do not lie inside it (AoS keeps the key inside the node).
+struct PoolSpan {
+    size_t next_bytes, key_bytes, prev_bytes;
+    bool key_inside;
+    ptrdiff_t key_off;
+};
+PoolSpan pool_span(const pbit_pool *p);
+
+// Tuned choices per (device, key width, size class), filled by the autotuner
+// and optionally persisted in the file named by PBIT_TUNE_FILE.
+bool tune_cache_lookup(int64_t pool_size, int32_t num_lists, int kb, pbit_tune *out);
+void tune_cache_store(int64_t pool_size, int32_t num_lists, int kb, const pbit_tune &t, float ms);
 
 }  // namespace pbit

@@ -123,6 +123,11 @@ struct Ctx {
     unsigned char *keyb[2];
     int32_t *idxb[2];
     int32_t *F;
+    // {next, sort key} packed per node in list-position order (8 bytes, 16
+    // for 64-bit keys) so the ranking walk makes one random access per hop;
+    // nullptr = the walk gathers next[] and key[] separately.  Aliases
+    // keyb[1] / idxb[1] / F, which are idle until the first pass.
+    unsigned char *pack;
     Seg *act[2];
     uint32_t *act_hist[2];      // seg_cap x 16 : histogram of the pass window
     int32_t *act_tile_base[2];  // seg_cap + 1
@@ -305,6 +310,7 @@ void prof_mark(const char *name, cudaStream_t s);
 // kernel entry points (defined in rank.cu / msd.cu / finish.cu)
 void launch_setup(const Ctx &c, const int64_t *d_offsets, const int32_t *d_roots, int mode,
                   const ListDesc *host_desc_tmpl, cudaStream_t s, int sms);
+void launch_pack(const Ctx &c, cudaStream_t s, int sms);
 void launch_walk(const Ctx &c, cudaStream_t s, int sms);
 void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds);
 void launch_validate_emit(const Ctx &c, int final_wy, cudaStream_t s, int sms);

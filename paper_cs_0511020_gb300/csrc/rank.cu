@@ -103,6 +103,44 @@ __global__ void __launch_bounds__(1024) k_setup(Ctx c, ListDesc t, const int64_t
     }
 }
 
+// ------------------------------------------------------------------- pack
+// One streaming pass over the pool: pack[p] = {next, sort key} of the node at
+// list position p's pool slot (p = out_base + local index), so the walk's
+// hop reads one 8-byte (or 16-byte) record instead of gathering next[] and
+// key[] from two arrays.  Shared pools map positions to nodes by one
+// constant shift; per-list pools (serving) look the list up.
+template <typename KeyT>
+__global__ void __launch_bounds__(256) k_pack(Ctx c) {
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int64_t nv = c.ctr->n_virt;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t lo = 0, hi = -1, shift = 0, ns = 4, ks = sizeof(KeyT);
+    const unsigned char *nb = nullptr, *kb = nullptr;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nv; p += stride) {
+        if (p >= hi || p < lo) {
+            const int32_t lst = c.shared_pool ? 0 : upper_index(c.out_base, c.num_lists, (int32_t)p);
+            const ListDesc &d = c.desc[lst];
+            lo = c.shared_pool ? 0 : d.out_base;
+            hi = c.shared_pool ? nv : (int64_t)d.out_base + d.n;
+            shift = (int64_t)d.id_base - d.out_base;
+            nb = reinterpret_cast<const unsigned char *>(d.next);
+            kb = d.key;
+            ns = d.next_stride;
+            ks = d.key_stride;
+        }
+        const int64_t node = p + shift;
+        const int32_t raw = *reinterpret_cast<const int32_t *>(nb + node * ns);
+        const KeyT k = sort_key<KeyT>(load_key_raw<KeyT>(kb + node * ks), c.flags, c.M);
+        if constexpr (sizeof(KeyT) == 8) {
+            reinterpret_cast<uint4 *>(c.pack)[p] =
+                make_uint4((uint32_t)raw, 0u, (uint32_t)(unsigned long long)k, (uint32_t)((unsigned long long)k >> 32));
+        } else {
+            reinterpret_cast<uint2 *>(c.pack)[p] = make_uint2((uint32_t)raw, (uint32_t)k);
+        }
+    }
+}
+
 // ------------------------------------------------------------------- walk
 // Every task (a ruler) walks next[] until the next ruler or NULL, one hop per
 // loop trip per lane; the key of each visited node is gathered in the same
@@ -261,21 +299,35 @@ __global__ void __launch_bounds__(256, 6) k_walk(Ctx c) {
             }
         }
         if (active) {
-            const int64_t node = (int64_t)(did + v);
             int32_t raw;
-            KeyT key;
-            if (aos) {
-                const uint2 nk = *reinterpret_cast<const uint2 *>(nxt + node * 8);
-                raw = (int32_t)nk.x;
-                key = (KeyT)nk.y;
+            KeyT skey;
+            if (c.pack) {  // one record per hop, the key already mapped
+                if constexpr (sizeof(KeyT) == 8) {
+                    const uint4 r = reinterpret_cast<const uint4 *>(c.pack)[dob + v];
+                    raw = (int32_t)r.x;
+                    skey = (KeyT)(((unsigned long long)r.w << 32) | r.z);
+                } else {
+                    const uint2 r = reinterpret_cast<const uint2 *>(c.pack)[dob + v];
+                    raw = (int32_t)r.x;
+                    skey = (KeyT)r.y;
+                }
             } else {
-                raw = *reinterpret_cast<const int32_t *>(nxt + node * nstride);
-                key = load_key_raw<KeyT>(kp + node * kstride);
+                const int64_t node = (int64_t)(did + v);
+                KeyT key;
+                if (aos) {
+                    const uint2 nk = *reinterpret_cast<const uint2 *>(nxt + node * 8);
+                    raw = (int32_t)nk.x;
+                    key = (KeyT)nk.y;
+                } else {
+                    raw = *reinterpret_cast<const int32_t *>(nxt + node * nstride);
+                    key = load_key_raw<KeyT>(kp + node * kstride);
+                }
+                skey = sort_key<KeyT>(key, c.flags, c.M);
             }
             const int e = j % CH;
             const int slot = e & (kStageN - 1);
             my_i[slot] = dob + v;
-            my_k[slot] = sort_key<KeyT>(key, c.flags, c.M);
+            my_k[slot] = skey;
             ++j;
             bool done = false;
             int32_t succ = -1;
@@ -435,6 +487,19 @@ void launch_setup(const Ctx &c, const int64_t *d_offsets, const int32_t *d_roots
         t = *tmpl;
     k_setup<<<1, 1024, 0, s>>>(c, t, d_offsets, d_roots, mode);
     prof_mark("setup", s);
+}
+
+void launch_pack(const Ctx &c, cudaStream_t s, int sms) {
+    if (!c.pack)
+        return;
+    const unsigned blocks = (unsigned)max((int64_t)1, min((int64_t)sms * 8, (c.ncap + 255) / 256));
+    switch (c.key_bytes) {
+    case 1: k_pack<uint8_t><<<blocks, 256, 0, s>>>(c); break;
+    case 2: k_pack<uint16_t><<<blocks, 256, 0, s>>>(c); break;
+    case 4: k_pack<uint32_t><<<blocks, 256, 0, s>>>(c); break;
+    default: k_pack<unsigned long long><<<blocks, 256, 0, s>>>(c); break;
+    }
+    prof_mark("pack", s);
 }
 
 void launch_walk(const Ctx &c, cudaStream_t s, int sms) {

@@ -31,7 +31,13 @@ struct SrvReq {
     bool solo = false;      // retry alone (its batch failed)
     int status = PBIT_EPENDING;
     int32_t new_root = -1;
+    int64_t submit_ns = 0, done_ns = 0;  // host steady clock
 };
+
+static int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
 
 struct SrvSlot {
     cudaStream_t stream = nullptr;
@@ -154,10 +160,12 @@ static void serve_loop(pbit_server *s) {
                 continue;
             const pbit_status st = map_status(slot.h_out[0]);
             if (st == PBIT_OK || slot.reqs.size() == 1) {
+                const int64_t t = now_ns();
                 for (size_t i = 0; i < slot.reqs.size(); ++i) {
                     SrvReq *r = slot.reqs[i];
                     r->status = st;
                     r->new_root = st == PBIT_OK ? slot.h_out[1 + i] : -1;
+                    r->done_ns = t;
                     ++s->completed;
                 }
             } else {  // isolate the failing request(s): retry each alone, in order
@@ -188,6 +196,7 @@ static void serve_loop(pbit_server *s) {
             if (rc != PBIT_OK) {
                 for (SrvReq *r : b) {
                     r->status = rc;
+                    r->done_ns = now_ns();
                     ++s->completed;
                 }
                 s->cv_done.notify_all();
@@ -263,6 +272,7 @@ pbit_status pbit_serve_submit(pbit_server *s, const pbit_pool *pool, int32_t roo
     r->n = n;
     r->M = M;
     r->K = K;
+    r->submit_ns = now_ns();
     {
         std::lock_guard<std::mutex> g(s->mu);
         r->ticket = s->next_ticket++;
@@ -271,6 +281,7 @@ pbit_status pbit_serve_submit(pbit_server *s, const pbit_pool *pool, int32_t roo
         if (n == 0) {  // an empty list is done at once (the paper returns NULL)
             r->status = PBIT_OK;
             r->new_root = -1;
+            r->done_ns = r->submit_ns;
             ++s->completed;
         } else {
             s->queue.push_back(r);
@@ -307,6 +318,34 @@ pbit_status pbit_serve_wait(pbit_server *s, uint64_t ticket, int32_t *new_root, 
     if (r->status == PBIT_OK && new_root)
         *new_root = r->new_root;
     return (pbit_status)r->status;
+}
+
+pbit_status pbit_serve_times(pbit_server *s, uint64_t ticket, int64_t *submit_ns, int64_t *done_ns) {
+    if (!s)
+        return PBIT_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+        return PBIT_EINVAL;
+    if (submit_ns)
+        *submit_ns = it->second->submit_ns;
+    if (done_ns)
+        *done_ns = it->second->done_ns;
+    return PBIT_OK;
+}
+
+pbit_status pbit_serve_release(pbit_server *s, uint64_t ticket) {
+    if (!s)
+        return PBIT_EINVAL;
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end())
+        return PBIT_EINVAL;
+    if (it->second->status == PBIT_EPENDING)
+        return PBIT_EPENDING;
+    delete it->second;
+    s->reqs.erase(it);
+    return PBIT_OK;
 }
 
 void pbit_serve_stats(pbit_server *s, int64_t *out5) {

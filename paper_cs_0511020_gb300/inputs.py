@@ -115,3 +115,62 @@ def config5_requests(count: int, seed: int):
     lengths = np.clip(np.floor(2.0 ** (4.0 + 20.0 * g.random(count))), 16, 1 << 24).astype(np.int64)
     kb = g.choice(np.array([2, 4, 4, 8]), size=count)
     return np.cumsum(gaps), lengths, kb
+
+
+# ---------------------------------------------------------------------------
+# Device-side generators for the benchmark's large workloads (same recipes,
+# drawn with torch's CUDA generator instead of numpy: 10^9 nodes are drawn in
+# seconds).  The parity tests use the numpy generators above.
+
+_TORCH_KEY = {2: "int16", 4: "int32", 8: "int64"}
+
+
+def device_keys(n: int, key_bytes: int, gen):
+    """Uniform keys over all 8*key_bytes bits, as a signed torch view."""
+    import torch
+    dt = getattr(torch, _TORCH_KEY.get(key_bytes, "uint8"))
+    if key_bytes == 1:
+        return torch.randint(0, 256, (n,), dtype=torch.uint8, device=gen.device, generator=gen)
+    if key_bytes == 8:
+        hi = torch.randint(-2**31, 2**31, (n,), dtype=torch.int64, device=gen.device, generator=gen)
+        lo = torch.randint(0, 2**32, (n,), dtype=torch.int64, device=gen.device, generator=gen)
+        return (hi << 32) | lo
+    lim = 1 << (8 * key_bytes - 1)
+    return torch.randint(-lim, lim, (n,), dtype=dt, device=gen.device, generator=gen)
+
+
+def device_random_list(n: int, gen):
+    """next[] (int32, on gen's device) of one list in a random order, and its root."""
+    import torch
+    perm = torch.randperm(n, dtype=torch.int64, device=gen.device, generator=gen)
+    nxt = torch.empty(n, dtype=torch.int32, device=gen.device)
+    nxt[perm[:-1]] = perm[1:].to(torch.int32)
+    nxt[perm[-1]] = -1
+    return nxt, int(perm[0])
+
+
+def device_batched_pool(lengths, key_bytes: int, gen):
+    """Lists packed into one pool (list i owns [off[i], off[i+1])), each in a
+    random order of its own range: (next, key, roots, offsets) on gen's device."""
+    import torch
+    dev = gen.device
+    lens = torch.as_tensor(np.asarray(lengths, dtype=np.int64), device=dev)
+    L = lens.numel()
+    off = torch.zeros(L + 1, dtype=torch.int64, device=dev)
+    off[1:] = torch.cumsum(lens, 0)
+    total = int(off[-1])
+    lid = torch.repeat_interleave(torch.arange(L, device=dev), lens)
+    # a random order inside every range: sort by (list id, random value)
+    r = torch.rand(total, dtype=torch.float64, device=dev, generator=gen)
+    order = torch.argsort(lid.to(torch.float64) * 2.0 + r)
+    nxt = torch.empty(total, dtype=torch.int32, device=dev)
+    last = off[1:] - 1                      # position of each list's tail in `order`
+    succ = torch.empty(total, dtype=torch.int64, device=dev)
+    succ[:-1] = order[1:]
+    succ[last[lens > 0]] = -1
+    nxt[order] = succ.to(torch.int32)
+    roots = torch.full((L,), -1, dtype=torch.int32, device=dev)
+    nz = lens > 0
+    roots[nz] = order[off[:-1][nz]].to(torch.int32)
+    key = device_keys(total, key_bytes, gen)
+    return nxt, key, roots, off

@@ -20,7 +20,10 @@ SIGNED, DESCENDING, DOUBLY, FLOAT = 1, 2, 4, 8
 EXPORTS = ("pbit_status_string", "pbit_workspace_size", "pbit_sort_list", "pbit_sort_lists_batched",
            "pbit_workspace_size_host", "pbit_sort_list_host", "pbit_sort_list_noalloc", "pbit_last_launch_count",
            "pbit_profile_enable", "pbit_profile_read", "pbit_serve_create", "pbit_serve_submit",
-           "pbit_serve_poll", "pbit_serve_wait", "pbit_serve_stats", "pbit_serve_destroy")
+           "pbit_serve_poll", "pbit_serve_wait", "pbit_serve_times", "pbit_serve_release", "pbit_serve_stats",
+           "pbit_serve_destroy", "pbit_graph_create_batched", "pbit_graph_create_single", "pbit_graph_launch",
+           "pbit_graph_result", "pbit_graph_node_count", "pbit_graph_destroy", "pbit_autotune_workspace_size",
+           "pbit_autotune_batched")
 
 
 class PbitError(RuntimeError):
@@ -44,7 +47,7 @@ class KernelStat(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_int32), ("smem_cutoff", ctypes.c_int32),
-                ("ruler_stride", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("ruler_stride", ctypes.c_int32), ("gather_pack", ctypes.c_int32)]
 
 
 _lib = None
@@ -88,6 +91,28 @@ def lib():
         L.pbit_serve_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32)]
         L.pbit_serve_wait.restype = ctypes.c_int
         L.pbit_serve_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32), i64]
+        L.pbit_serve_times.restype = ctypes.c_int
+        L.pbit_serve_times.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.pbit_serve_release.restype = ctypes.c_int
+        L.pbit_serve_release.argtypes = [vp, ctypes.c_uint64]
+        L.pbit_graph_create_batched.restype = ctypes.c_int
+        L.pbit_graph_create_batched.argtypes = [vp, i32, vp, vp, i32, i32, vp, vp, vp, ctypes.c_size_t,
+                                                ctypes.POINTER(vp)]
+        L.pbit_graph_create_single.restype = ctypes.c_int
+        L.pbit_graph_create_single.argtypes = [vp, i32, i64, i32, i32, vp, vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+        L.pbit_graph_launch.restype = ctypes.c_int
+        L.pbit_graph_launch.argtypes = [vp, vp]
+        L.pbit_graph_result.restype = ctypes.c_int
+        L.pbit_graph_result.argtypes = [vp, vp, ctypes.POINTER(i32)]
+        L.pbit_graph_node_count.restype = i64
+        L.pbit_graph_node_count.argtypes = [vp]
+        L.pbit_graph_destroy.restype = None
+        L.pbit_graph_destroy.argtypes = [vp]
+        L.pbit_autotune_workspace_size.restype = ctypes.c_int
+        L.pbit_autotune_workspace_size.argtypes = [i64, i32, i32, ctypes.POINTER(ctypes.c_size_t)]
+        L.pbit_autotune_batched.restype = ctypes.c_int
+        L.pbit_autotune_batched.argtypes = [vp, i32, vp, vp, i32, i32, vp, vp, ctypes.c_size_t, i32, vp, vp,
+                                            ctypes.POINTER(ctypes.c_float)]
         L.pbit_serve_stats.restype = None
         L.pbit_serve_stats.argtypes = [vp, ctypes.POINTER(i64)]
         L.pbit_serve_destroy.restype = None
@@ -110,7 +135,8 @@ def _tune_ptr(tune):
     if tune is None:
         return None, None
     if isinstance(tune, dict):
-        tune = Tune(tune.get("digit_bits", 0), tune.get("smem_cutoff", 0), tune.get("ruler_stride", 0), 0)
+        tune = Tune(tune.get("digit_bits", 0), tune.get("smem_cutoff", 0), tune.get("ruler_stride", 0),
+                    tune.get("gather_pack", 0))
     return tune, ctypes.addressof(tune)
 
 
@@ -264,6 +290,105 @@ def sort_pool_list_host(pool: Pool, root: int, n: int, M: int, K: int = 4, ws=No
     return st, int(nr.value)
 
 
+class Graph:
+    """A sort call captured once as a CUDA graph (pbit_graph_*) and replayed.
+
+    Keeps references to every tensor the graph points at (pool arrays,
+    roots, offsets, new roots, workspace) so they stay allocated."""
+
+    def __init__(self, handle, keep, single: bool):
+        self._h = handle
+        self._keep = keep
+        self.single = single
+
+    @classmethod
+    def batched(cls, pool: Pool, roots_t: torch.Tensor, offsets_t: torch.Tensor, M: int, K: int = 4,
+                new_roots_t: torch.Tensor | None = None, ws=None, tune=None, keep=()):
+        assert roots_t.dtype == torch.int32 and offsets_t.dtype == torch.int64
+        L = roots_t.numel()
+        assert offsets_t.numel() == L + 1
+        if new_roots_t is None:
+            new_roots_t = torch.empty(L, dtype=torch.int32, device=roots_t.device)
+        if ws is None:
+            ws = alloc_workspace(workspace_size(pool.pool_size, L, pool.key_type, tune))
+        tune_s, tp = _tune_ptr(tune)
+        h = ctypes.c_void_p()
+        st = lib().pbit_graph_create_batched(ctypes.addressof(pool), L, roots_t.data_ptr(), offsets_t.data_ptr(),
+                                             int(M), int(K), new_roots_t.data_ptr(), tp, ws.data_ptr(), ws.numel(),
+                                             ctypes.byref(h))
+        if st != OK:
+            raise PbitError(st, "pbit_graph_create_batched")
+        g = cls(h, (pool, roots_t, offsets_t, ws, tune_s, keep), False)
+        g.new_roots = new_roots_t
+        return g
+
+    @classmethod
+    def single_list(cls, pool: Pool, root: int, n: int, M: int, K: int = 4, ws=None, tune=None, keep=()):
+        if ws is None:
+            ws = alloc_workspace(workspace_size(pool.pool_size, 1, pool.key_type, tune))
+        tune_s, tp = _tune_ptr(tune)
+        h = ctypes.c_void_p()
+        st = lib().pbit_graph_create_single(ctypes.addressof(pool), int(root), int(n), int(M), int(K), tp,
+                                            ws.data_ptr(), ws.numel(), ctypes.byref(h))
+        if st != OK:
+            raise PbitError(st, "pbit_graph_create_single")
+        return cls(h, (pool, ws, tune_s, keep), True)
+
+    def launch(self, stream=None) -> None:
+        st = lib().pbit_graph_launch(self._h, _stream_handle(stream))
+        if st != OK:
+            raise PbitError(st, "pbit_graph_launch")
+
+    def result(self, stream=None, check: bool = True):
+        """(status, new_root) of the last replay; new_root is -1 for a batched graph."""
+        nr = ctypes.c_int32(-1)
+        st = lib().pbit_graph_result(self._h, _stream_handle(stream), ctypes.byref(nr))
+        if check and st != OK:
+            raise PbitError(st, "pbit_graph_result")
+        return st, int(nr.value)
+
+    def node_count(self) -> int:
+        return int(lib().pbit_graph_node_count(self._h))
+
+    def close(self):
+        if self._h:
+            lib().pbit_graph_destroy(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune_workspace_size(pool_size: int, num_lists: int, key_bytes: int) -> int:
+    out = ctypes.c_size_t(0)
+    st = lib().pbit_autotune_workspace_size(int(pool_size), int(num_lists), int(key_bytes), ctypes.byref(out))
+    if st != OK:
+        raise PbitError(st, "pbit_autotune_workspace_size")
+    return int(out.value)
+
+
+def autotune_batched(pool: Pool, roots_t: torch.Tensor, offsets_t: torch.Tensor, M: int, K: int = 4,
+                     reps: int = 3, ws=None, stream=None):
+    """pbit_autotune_batched: returns ({smem_cutoff, ruler_stride, digit_bits}, median ms).
+    The pool is left in its input state."""
+    L = roots_t.numel()
+    new_roots_t = torch.empty(L, dtype=torch.int32, device=roots_t.device)
+    if ws is None:
+        ws = alloc_workspace(autotune_workspace_size(pool.pool_size, L, pool.key_type))
+    best = Tune()
+    ms = ctypes.c_float(0)
+    st = lib().pbit_autotune_batched(ctypes.addressof(pool), L, roots_t.data_ptr(), offsets_t.data_ptr(), int(M),
+                                     int(K), new_roots_t.data_ptr(), ws.data_ptr(), ws.numel(), int(reps),
+                                     _stream_handle(stream), ctypes.addressof(best), ctypes.byref(ms))
+    if st != OK:
+        raise PbitError(st, "pbit_autotune_batched")
+    return dict(digit_bits=best.digit_bits, smem_cutoff=best.smem_cutoff, ruler_stride=best.ruler_stride), ms.value
+
+
 class Server:
     """Request server (pbit_serve_*): continuous batching of sort requests
     whose pools the caller keeps alive until they finish."""
@@ -296,6 +421,21 @@ class Server:
         nr = ctypes.c_int32(-7)
         st = lib().pbit_serve_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(nr), int(timeout_ms))
         return st, int(nr.value)
+
+    def times(self, ticket: int):
+        """(submit_ns, done_ns) on the host steady clock; done_ns is 0 while pending."""
+        a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+        st = lib().pbit_serve_times(self._h, ctypes.c_uint64(ticket), ctypes.byref(a), ctypes.byref(b))
+        if st != OK:
+            raise PbitError(st, "pbit_serve_times")
+        return int(a.value), int(b.value)
+
+    def release(self, ticket: int) -> int:
+        """Forget a finished ticket and drop the references kept for it."""
+        st = lib().pbit_serve_release(self._h, ctypes.c_uint64(ticket))
+        if st == OK:
+            self._keep.pop(ticket, None)
+        return st
 
     def stats(self) -> dict:
         a = (ctypes.c_int64 * 5)()

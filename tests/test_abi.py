@@ -70,7 +70,8 @@ def test_tune_validation(so):
     f.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
     out = ctypes.c_size_t(0)
     for tune, ok in (((4, 0, 0, 0), True), ((8, 0, 0, 0), False), ((0, 512, 0, 0), True), ((0, 513, 0, 0), False),
-                     ((0, 0, 64, 0), True), ((0, 0, 48, 0), False), ((0, 0, 1 << 13, 0), False)):
+                     ((0, 0, 64, 0), True), ((0, 0, 48, 0), False), ((0, 0, 1 << 13, 0), False),
+                     ((0, 0, 0, 2), True), ((0, 0, 0, 3), False), ((0, 0, 0, -1), False)):
         t = pbit.Tune(*tune)
         assert (f(1 << 20, 1, 4, ctypes.addressof(t), ctypes.byref(out)) == 0) == ok, tune
 
@@ -92,3 +93,46 @@ def test_sort_rejects_bad_arguments_without_touching_the_device(so):
     assert nr.value == -1
     signed_m = pbit.Pool(0x1000, 4, 0x2000, 4, 4, pbit.SIGNED, 10, 0, 0)
     assert f(ctypes.addressof(signed_m), 0, 10, 16, 4, ctypes.byref(nr), None, None, 0, None) == 1
+
+
+def test_autotune_workspace_covers_every_candidate(so):
+    from paper_cs_0511020_gb300 import pbit
+    n, L = 1 << 22, 64
+    big = pbit.autotune_workspace_size(n, L, 4)
+    for c in (128, 256, 512):
+        for r in (16, 32, 64, 128):
+            assert big >= pbit.workspace_size(n, L, 4, {"smem_cutoff": c, "ruler_stride": r})
+    assert big >= pbit.workspace_size(n, L, 4)
+
+
+_TUNE_PROBE = """
+import json
+from paper_cs_0511020_gb300 import pbit
+n = 1 << 20
+print(json.dumps([pbit.workspace_size(n, 1, 4), pbit.workspace_size(n, 1, 4, {"smem_cutoff": 128, "ruler_stride": 16}),
+                  pbit.workspace_size(n, 1, 4, {"smem_cutoff": 512, "ruler_stride": 32}),
+                  pbit.workspace_size(1 << 24, 1, 4),
+                  pbit.workspace_size(1 << 24, 1, 4, {"smem_cutoff": 512, "ruler_stride": 32})]))
+"""
+
+
+def test_tune_file_is_read_for_its_size_class(so, tmp_path):
+    """A tuned choice stored in PBIT_TUNE_FILE is taken (tune = NULL) for its
+    size class only: the workspace size then leaves room for it.  Host logic
+    only: without a device the library keys entries by its fallback SM count
+    148 and compute capability 0."""
+    import json
+    import subprocess
+    import sys
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("device present: the entry below is keyed for the no-device fallback")
+    f = tmp_path / "tune.txt"
+    f.write_text("garbage line\npbit-tune sms=148 cc=0 kb=4 lg_n=20 lg_l=0 cutoff=128 stride=16 ms=1.5\n")
+    env = dict(os.environ, PBIT_TUNE_FILE=str(f))
+    out = subprocess.run([sys.executable, "-c", _TUNE_PROBE], env=env, cwd=ROOT, capture_output=True, text=True,
+                         check=True).stdout
+    none_20, tuned_20, default_20, none_24, default_24 = json.loads(out.strip().splitlines()[-1])
+    assert tuned_20 > default_20
+    assert none_20 == tuned_20          # room for the stored choice
+    assert none_24 == default_24        # another size class: built-in default

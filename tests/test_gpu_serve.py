@@ -108,3 +108,24 @@ def test_serve_budget_and_empty(pb):
         assert srv.wait(t, 1000) == (pb.OK, -1)
     finally:
         srv.close()
+
+
+def test_serve_times_and_release(pb):
+    srv = pb.Server(mem_budget_bytes=1 << 30, streams=2, max_batch=8)
+    try:
+        items = []
+        for i in range(5):
+            n = 5000 + i
+            nxt, root = I.random_list(n, 800 + i)
+            d_next, d_key = torch.from_numpy(nxt.copy()).cuda(), _dev(I.uniform_keys(n, 4, 810 + i))
+            torch.cuda.synchronize()
+            items.append(srv.submit(pb.make_pool(d_next, d_key), root, n, 32, 4, keep=(d_next, d_key)))
+        for t in items:
+            assert srv.wait(t, 60000)[0] == pb.OK
+            sub, done = srv.times(t)
+            assert 0 < sub <= done
+            assert srv.release(t) == pb.OK
+            assert srv.poll(t)[0] == pb.EINVAL
+            assert srv.release(t) == pb.EINVAL
+    finally:
+        srv.close()

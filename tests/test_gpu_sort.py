@@ -261,3 +261,39 @@ def test_constant_windows(pb, pattern):
         key = (g.integers(0, 5, n, dtype=np.uint64) << np.uint64(50)) | \
             (g.integers(0, 1 << 20, n, dtype=np.uint64) << np.uint64(3))
     _check_vs_oracle(pb, nxt, key, root, 8 * key.itemsize)
+
+
+@pytest.mark.parametrize("pack", [1, 2])
+@pytest.mark.parametrize("case", ["u8", "u16", "u32", "u64", "signed", "float64", "aos"])
+def test_gather_pack_on_and_off(pb, case, pack):
+    """The ranking walk reads {next, sort key} records packed by a pre-pass
+    (gather_pack = 2) or gathers next[] and key[] itself (1): same result."""
+    n = 150001
+    nxt, root = I.random_list(n, 171)
+    tune = {"gather_pack": pack}
+    if case == "aos":
+        key = I.uniform_keys(n, 4, 172)
+        nodes = torch.from_numpy(I.aos_pack(nxt, key)).cuda()
+        st, r = pb.sort_pool_list(pb.make_pool_aos(nodes), root, n, 32, 4, tune=tune, check=False)
+        want, wr, _ = O.pbit_sort(nxt, key, root, 32, 4)
+        assert st == pb.OK and r == wr and (nodes[:, 0].cpu().numpy() == want).all()
+        return
+    if case in ("signed", "float64"):
+        if case == "signed":
+            key = I.uniform_keys(n, 4, 173)
+            flags = pb.SIGNED
+            want, wr = O.stable_sort_definition(nxt, key, root, 32, signed=True)
+        else:
+            vals = I.rng(174).standard_normal(n)
+            vals[::7] = 0.0
+            key = vals.view(np.uint64)
+            flags = pb.FLOAT
+            order_in = O.list_order(nxt, root)
+            v = vals[order_in]
+            perm = np.lexsort((np.arange(n), np.signbit(v) == False, v))  # noqa: E712
+            want, wr = O.relink(nxt, order_in[perm])
+        st, got, r = _gpu_sort(pb, nxt, key, root, 8 * key.itemsize, 4, flags=flags, tune=tune)
+        assert st == pb.OK and r == wr and (got == want).all()
+        return
+    kb = {"u8": 1, "u16": 2, "u32": 4, "u64": 8}[case]
+    _check_vs_oracle(pb, nxt, I.uniform_keys(n, kb, 175 + kb), root, 8 * kb, tune=tune)
