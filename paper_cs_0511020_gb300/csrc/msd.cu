@@ -523,11 +523,12 @@ __global__ void __launch_bounds__(kTPB) k_chunk_scan(Ctx c, int it) {
 
 // ------------------------------------------------------------------ pass
 struct PassSmem {
-    uint32_t wcnt[kTPB / 32][kBins];  // per-warp digit counts -> exclusive prefixes
+    uint32_t wcnt[kTPB / 32][kBins];  // per-warp digit counts -> tile positions of each warp's digits
     uint32_t tile_off[kBins + 1];
     uint32_t tile_cnt[kBins];
-    int32_t gbase[kBins];
-    int32_t bstart[kBins];            // start of each output bucket
+    int32_t gbase[kBins];             // output position of this tile's first element of each digit
+    int32_t gdelta[kBins];            // gbase - tile offset: output position = gdelta + tile position
+    int32_t split[kBins];             // first output position in next-pass tile k0 + 1
     int32_t nrow[kBins];              // first next-pass row of each output bucket
     int32_t k0[kBins];                // next-pass tile of this tile's first element per bucket
     uint32_t nc[kBins * 2 * kBins];   // counts per (bucket, next tile k0/k0+1, next digit)
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
     }
     if (tid == 0)
         S.aseg = -1;
-    uint32_t phase[2] = {0, 0};
+    uint32_t phases = 0;  // bit b: parity of stage b's barrier
     int st = 0;
     if (tid == 0) {
         const int g = atomicAdd(&c.ctr->tile_ctr[it], 1);
@@ -659,9 +660,11 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                 const int ch = c.act_chunk_base[cur][s] + k / kScanRows;
                 before = c.ctot[(int64_t)ch * kBins + d] + c.tcnt[cur][((int64_t)sg.row + k) * kBins + d];
             }
-            S.bstart[d] = sg.start + (int32_t)ex;
-            S.gbase[d] = sg.start + (int32_t)ex + (int32_t)before;
-            S.k0[d] = (int32_t)(before >> kTileLog);
+            const int32_t bst = sg.start + (int32_t)ex;  // start of output bucket d
+            const int32_t k0 = (int32_t)(before >> kTileLog);
+            S.gbase[d] = bst + (int32_t)before;
+            S.k0[d] = k0;
+            S.split[d] = bst + ((k0 + 1) << kTileLog);  // first position of next-pass tile k0 + 1
             S.nrow[d] = c.act_nrow_base[cur][s] + (int32_t)nt_d;
             const int as = S.aseg;
             if (as != s) {  // new segment: flush the merged AND/OR of the previous one
@@ -676,35 +679,39 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
             if (d == 0)
                 S.aseg = s;
         }
+        uint32_t *wc = S.wcnt[wid];  // this warp's digit counts, then its digits' tile positions
         // one thread waits for the copy (acquire), the barrier then publishes
         // the tile to the whole CTA
-        const bool landed = (tid != 0) || mbar_wait_bounded(&S.bar[st], phase[st], 1ll << 26);
+        const bool landed = (tid != 0) || mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
         if (!__syncthreads_and(landed)) {
             set_status(c.status, PBIT_ETIMEOUT);
             if (tid == 0) {  // wait (bounded) for the copies still in flight before leaving
-                mbar_wait_bounded(&S.bar[st], phase[st], 1ll << 26);
+                mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
                 if (S.nt[st ^ 1] < ntiles)
-                    mbar_wait_bounded(&S.bar[st ^ 1], phase[st ^ 1], 1ll << 26);
+                    mbar_wait_bounded(&S.bar[st ^ 1], (phases >> (st ^ 1)) & 1u, 1ll << 26);
             }
             return;
         }
-        phase[st] ^= 1;
+        phases ^= 1u << st;
         const unsigned dmask = (1u << (hi - lo)) - 1u;
         const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + S.st_shk[st];
         const int32_t *si = reinterpret_cast<const int32_t *>(stage + PassLayout<KeyT>::kKeyBytes) + S.st_shi[st];
 
-        // ---- load + warp-ballot ranking (order: warp, item, lane == memory order)
+        // ---- load + warp-ballot ranking (order: warp, item, lane == memory order).
+        // Four ballots give each lane the lanes holding its digit (peers) and
+        // lane d < 16 the count of digit d in the item (mine); lane d keeps the
+        // running count of digit d over the warp's earlier items.
         KeyT key[kItems];
         int32_t idx[kItems];
         uint32_t rnk[kItems];
-        uint32_t run = 0;  // lane d < 16: count of digit d in this warp so far
+        uint32_t run = 0;
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const int pos = wid * (32 * kItems) + i * 32 + lane;
             const bool valid = pos < cnt;
             key[i] = valid ? sk[pos] : (KeyT)0;
             idx[i] = valid ? si[pos] : 0;
-            const unsigned dig = valid ? (unsigned)((unsigned long long)key[i] >> lo) & dmask : 0u;
+            const unsigned dig = valid ? digit_of<KeyT>(key[i], lo, dmask) : 0u;
             const unsigned vm = __ballot_sync(kFull, valid);
             unsigned peers = vm, mine = vm;
 #pragma unroll
@@ -713,35 +720,34 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                 peers &= ((dig >> b) & 1u) ? bb : ~bb;
                 mine &= ((lane >> b) & 1) ? bb : ~bb;
             }
-            rnk[i] = __shfl_sync(kFull, run, (int)dig) + __popc(peers & lt);
-            run += __popc(mine);
+            rnk[i] = __shfl_sync(kFull, run, (int)dig) + (uint32_t)__popc(peers & lt);
+            run += (uint32_t)__popc(mine);
         }
         if (lane < kBins)
-            S.wcnt[wid][lane] = run;
+            wc[lane] = run;
         __syncthreads();
-        if (wid == 0) {  // tile histogram and prefixes
-            const int d = lane & (kBins - 1);
+        if (wid == 0 && lane < kBins) {  // tile histogram, digit offsets, per-warp bases
+            const int d = lane;
             uint32_t tot = 0;
-            if (lane < kBins) {
 #pragma unroll
-                for (int w = 0; w < kTPB / 32; ++w) {
-                    const uint32_t x = S.wcnt[w][d];
-                    S.wcnt[w][d] = tot;
-                    tot += x;
-                }
-                S.tile_cnt[d] = tot;
-            }
-            uint32_t incl = (lane < kBins) ? tot : 0u;
+            for (int w = 0; w < kTPB / 32; ++w)
+                tot += S.wcnt[w][d];
+            uint32_t incl = tot;
 #pragma unroll
             for (int o = 1; o < kBins; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o)
+                const uint32_t y = __shfl_up_sync(0xffffu, incl, o);
+                if (d >= o)
                     incl += y;
             }
-            if (lane < kBins) {
-                S.tile_off[d] = incl - tot;
-                if (d == kBins - 1)
-                    S.tile_off[kBins] = incl;
+            uint32_t run = incl - tot;  // tile offset of digit d
+            S.tile_off[d] = run;
+            S.tile_cnt[d] = tot;
+            S.gdelta[d] = S.gbase[d] - (int32_t)run;
+#pragma unroll
+            for (int w = 0; w < kTPB / 32; ++w) {
+                const uint32_t x = S.wcnt[w][d];
+                S.wcnt[w][d] = run;
+                run += x;
             }
         }
         __syncthreads();
@@ -752,52 +758,57 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
         for (int i = 0; i < kItems; ++i) {
             const int pos = wid * (32 * kItems) + i * 32 + lane;
             if (pos < cnt) {
-                const unsigned dig = (unsigned)((unsigned long long)key[i] >> lo) & dmask;
-                const uint32_t lp = S.tile_off[dig] + S.wcnt[wid][dig] + rnk[i];
+                const uint32_t lp = wc[digit_of<KeyT>(key[i], lo, dmask)] + rnk[i];
                 ok[lp] = key[i];
                 oi[lp] = idx[i];
             }
         }
         __syncthreads();
         // ---- coalesced write-out (+ counts of the next pass's tiles)
-        const int seg_end = sg.start + sg.len;
         KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(sg.buf & 1) ^ 1]);
         int32_t *oidx = c.idxb[(sg.buf & 1) ^ 1];
         if (lo == 0 || sg.final) {
-            for (int j = tid; j < cnt; j += kTPB) {
-                const unsigned dig = (unsigned)((unsigned long long)ok[j] >> lo) & dmask;
-                const int dst = S.gbase[dig] + (j - (int)S.tile_off[dig]);
-                if (dst < sg.start || dst >= seg_end) {
-                    set_status(c.status, kStOverflow);
-                    continue;
+#pragma unroll
+            for (int u = 0; u < kItems; ++u) {
+                const int j = u * kTPB + tid;
+                if (j < cnt) {
+                    const int dst = S.gdelta[digit_of<KeyT>(ok[j], lo, dmask)] + j;
+                    if ((unsigned)(dst - sg.start) >= (unsigned)sg.len)
+                        set_status(c.status, kStOverflow);
+                    else
+                        c.F[dst] = oi[j];
                 }
-                c.F[dst] = oi[j];
             }
         } else {
             const int nlo = max(lo - kD, 0);
             const unsigned nmask = (1u << (lo - nlo)) - 1u;
-            for (int j = tid; j < cnt; j += kTPB) {
-                const KeyT kk = ok[j];
-                const unsigned dig = (unsigned)((unsigned long long)kk >> lo) & dmask;
-                const int dst = S.gbase[dig] + (j - (int)S.tile_off[dig]);
-                if (dst < sg.start || dst >= seg_end) {
-                    set_status(c.status, kStOverflow);
-                    continue;
+#pragma unroll
+            for (int u = 0; u < kItems; ++u) {
+                const int j = u * kTPB + tid;
+                if (j < cnt) {
+                    const KeyT kk = ok[j];
+                    const unsigned dig = digit_of<KeyT>(kk, lo, dmask);
+                    const int dst = S.gdelta[dig] + j;
+                    if ((unsigned)(dst - sg.start) >= (unsigned)sg.len) {
+                        set_status(c.status, kStOverflow);
+                    } else {
+                        okey[dst] = kk;
+                        oidx[dst] = oi[j];
+                        const unsigned nd = digit_of<KeyT>(kk, nlo, nmask);
+                        const unsigned kk1 = dst >= S.split[dig] ? 1u : 0u;  // next-pass tile k0 or k0 + 1
+                        atomicAdd(&S.nc[(dig * 2 + kk1) * kBins + nd], 1u);
+                    }
                 }
-                okey[dst] = kk;
-                oidx[dst] = oi[j];
-                const unsigned nd = (unsigned)((unsigned long long)kk >> nlo) & nmask;
-                const int kk1 = ((dst - S.bstart[dig]) >> kTileLog) - S.k0[dig];  // 0 or 1
-                atomicAdd(&S.nc[(dig * 2 + kk1) * kBins + nd], 1u);
             }
             // AND/OR of every output bucket: warp wid handles digits wid, wid+8
+            using U = typename KeyWord<KeyT>::U;
             for (int d = wid; d < kBins; d += kTPB / 32) {
                 const int b0 = (int)S.tile_off[d], n0 = (int)S.tile_cnt[d];
                 if (n0 == 0)
                     continue;
-                unsigned long long aa = ~0ull, oo = 0ull;
+                U aa = ~(U)0, oo = 0;
                 for (int j = lane; j < n0; j += 32) {
-                    const unsigned long long kk = (unsigned long long)ok[b0 + j];
+                    const U kk = (U)ok[b0 + j];
                     aa &= kk;
                     oo |= kk;
                 }
@@ -806,9 +817,9 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                     aa &= __shfl_xor_sync(kFull, aa, o);
                     oo |= __shfl_xor_sync(kFull, oo, o);
                 }
-                if (lane == 0) {
-                    S.aand[d] &= aa;  // this warp alone owns digit d here
-                    S.aor[d] |= oo;
+                if (lane == 0) {  // keys are zero-extended to 64 bits, as in seg_stats
+                    S.aand[d] &= (unsigned long long)aa;
+                    S.aor[d] |= (unsigned long long)oo;
                 }
             }
             __syncthreads();

@@ -1,6 +1,7 @@
 // pbit_internal.cuh -- device-side layout and helpers shared by the kernels of
 // the GB300 Pbit list sort.  Host orchestration is in engine.cu.
 #pragma once
+#include <type_traits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -195,6 +196,17 @@ __device__ __forceinline__ int32_t upper_index(const int32_t *a, int32_t n, int3
     return lo;
 }
 
+// Keys up to 32 bits are handled in 32-bit words (digit shifts, AND/OR).
+template <typename KeyT>
+struct KeyWord {
+    using U = typename std::conditional<sizeof(KeyT) <= 4, uint32_t, unsigned long long>::type;
+};
+
+template <typename KeyT>
+__device__ __forceinline__ unsigned digit_of(KeyT k, int lo, unsigned mask) {
+    return (unsigned)((typename KeyWord<KeyT>::U)k >> lo) & mask;
+}
+
 template <typename KeyT>
 __device__ __forceinline__ KeyT load_key_raw(const unsigned char *p) {
     return *reinterpret_cast<const KeyT *>(p);
@@ -220,6 +232,21 @@ __device__ __forceinline__ KeyT sort_key(KeyT k, int flags, int M) {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+// Per-thread asynchronous global -> shared copies (4 or 8 bytes, aligned to
+// their size); a thread waits for its own copies, a barrier then publishes
+// them to the others.
+template <int kBytes>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    static_assert(kBytes == 4 || kBytes == 8, "cp.async size");
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    if constexpr (kBytes == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
