@@ -1,6 +1,6 @@
 // finish.cu -- stages (c) and (d).
 //
-// (c) Small buckets are finished in registers.  In the paper the recursion
+// (c) Small buckets are finished in registers or shared memory.  In the paper the recursion
 //     runs every bucket down to M == 0 and merge() then appends the leaf
 //     buckets (Sec. "Implementation in C++", Sec. 5.1); the paper itself notes
 //     that MSD sorting spends too long on small chunks (Sec. "Differences
@@ -24,12 +24,245 @@ constexpr int kFD = 4;
 constexpr int kFBins = 1 << kFD;
 constexpr int kFWarps = 4;               // warps per finish CTA
 
-// One warp per bucket.  The bucket lives in the warp's two shared-memory
-// buffers; every window is two sweeps over its 32-element groups: count the
+constexpr int kNetMax = 256;  // buckets up to this size are sorted by a register network
+
+// Warp-wide bitonic sorting network over N values held in registers (lane l
+// holds the values at positions l, 32 + l, ...): stage (k, s) compares the
+// values at positions e and e ^ s and leaves the smaller at the lower
+// position when e & k == 0 (the larger otherwise).  Exchanges across lanes
+// go through shuffles, exchanges within a lane are register swaps.
+template <typename C, int N>
+__device__ __forceinline__ void warp_bitonic(C (&c)[N / 32], int lane) {
+    constexpr int J = N / 32;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int s = k >> 1; s > 0; s >>= 1) {
+            if (s >= 32) {
+                const int js = s >> 5;
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    if ((j & js) == 0) {
+                        const bool asc = ((j * 32) & k) == 0;  // k > 32 here: lane bits do not matter
+                        const C x = c[j], y = c[j | js];
+                        const C lo = x < y ? x : y, hi = x < y ? y : x;
+                        c[j] = asc ? lo : hi;
+                        c[j | js] = asc ? hi : lo;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const C o = __shfl_xor_sync(kFull, c[j], s);
+                    const bool keep_lo = ((lane & s) == 0) == (((j * 32 + lane) & k) == 0);
+                    const C lo = c[j] < o ? c[j] : o, hi = c[j] < o ? o : c[j];
+                    c[j] = keep_lo ? lo : hi;
+                }
+            }
+        }
+    }
+}
+
+// Sort a bucket of len <= N nodes with the network: the sort key of a node is
+// (its varying key bits, its position in the bucket) -- unique, so the
+// network's order is the stable order -- and after the sort each slot's
+// position field names the node whose id goes there.  Returns false (nothing
+// written) when the varying bits and the position do not fit in 64 bits.
+template <typename KeyT, int N, typename C>
+__device__ __forceinline__ void net_sort(const KeyT (&k)[N / 32], const int32_t *is, int32_t *dst, int len,
+                                         int lv, int sbits, int lane) {
+    constexpr int J = N / 32;
+    constexpr int PB = N == 32 ? 5 : (N == 64 ? 6 : (N == 128 ? 7 : 8));
+    const unsigned long long smask = sbits >= 64 ? ~0ull : ((1ull << sbits) - 1ull);
+    C c[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int e = j * 32 + lane;
+        c[j] = e < len ? (C)(((((unsigned long long)k[j] >> lv) & smask) << PB) | (unsigned long long)e) : ~(C)0;
+    }
+    warp_bitonic<C, N>(c, lane);
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int e = j * 32 + lane;
+        if (e < len)
+            dst[e] = is[(int)(c[j] & (C)(N - 1))];
+    }
+}
+
+template <typename KeyT, int N>
+__device__ __forceinline__ bool net_bucket(const KeyT *ks, const int32_t *is, int32_t *dst, int len, int hi,
+                                           int lane) {
+    constexpr int J = N / 32;
+    constexpr int PB = N == 32 ? 5 : (N == 64 ? 6 : (N == 128 ? 7 : 8));
+    using U = typename KeyWord<KeyT>::U;
+    KeyT k[J];
+    U a_and = ~(U)0, a_or = 0;
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        const int e = j * 32 + lane;
+        k[j] = 0;
+        if (e < len) {
+            k[j] = ks[e];
+            a_and &= (U)k[j];
+            a_or |= (U)k[j];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a_and &= __shfl_xor_sync(kFull, a_and, o);
+        a_or |= __shfl_xor_sync(kFull, a_or, o);
+    }
+    const unsigned long long vary =
+        (unsigned long long)(a_and ^ a_or) & (hi >= 64 ? ~0ull : ((1ull << hi) - 1ull));
+    if (!vary) {  // every key agrees on the remaining bits: list order stands
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int e = j * 32 + lane;
+            if (e < len)
+                dst[e] = is[e];
+        }
+        return true;
+    }
+    const int lv = __ffsll((long long)vary) - 1, hv = 63 - __clzll((long long)vary);
+    const int sbits = hv - lv + 1;
+    if (sbits + PB <= 32)
+        net_sort<KeyT, N, uint32_t>(k, is, dst, len, lv, sbits, lane);
+    else if (sbits + PB <= 64)
+        net_sort<KeyT, N, unsigned long long>(k, is, dst, len, lv, sbits, lane);
+    else
+        return false;
+    return true;
+}
+
+template <typename KeyT>
+__device__ __forceinline__ bool net_finish(const KeyT *ks, const int32_t *is, int32_t *dst, int len, int hi,
+                                           int lane) {
+    if (len <= 32)
+        return net_bucket<KeyT, 32>(ks, is, dst, len, hi, lane);
+    if (len <= 64)
+        return net_bucket<KeyT, 64>(ks, is, dst, len, hi, lane);
+    if (len <= 128)
+        return net_bucket<KeyT, 128>(ks, is, dst, len, hi, lane);
+    return net_bucket<KeyT, 256>(ks, is, dst, len, hi, lane);
+}
+
+// Larger buckets (and keys whose varying bits are too wide for the network's
+// sort key) are sorted in the warp's two shared-memory buffers by counting
+// passes: every window is two sweeps over its 32-element groups, count the
 // digits (4 ballots per group), then rank each group again and scatter it to
-// the other buffer at its digit's offset.  Keeping the keys in shared memory
-// instead of registers leaves room for many warps per SM, which is what hides
-// the load latency of one small bucket after another.
+// the other buffer at its digit's offset.
+template <typename KeyT>
+__device__ __forceinline__ void lsd_bucket(const KeyT *src_key, const int32_t *src_idx, int32_t *dst, int len,
+                                           int hi, KeyT *sk0, int32_t *si0, int lane, unsigned lt) {
+    const int ng = (len + 31) >> 5;  // 32-element groups (warp-uniform)
+    int a = 0;                        // buffer holding the current order
+    unsigned long long a_and = ~0ull, a_or = 0ull;
+    for (int g = 0; g < ng; ++g) {
+        const int pos = g * 32 + lane;
+        if (pos < len) {
+            const KeyT k = src_key[pos];
+            sk0[pos] = k;
+            si0[pos] = src_idx[pos];
+            a_and &= (unsigned long long)k;
+            a_or |= (unsigned long long)k;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a_and &= __shfl_xor_sync(kFull, a_and, o);
+        a_or |= __shfl_xor_sync(kFull, a_or, o);
+    }
+    __syncwarp();
+    const unsigned long long vary = (a_and ^ a_or) & (hi >= 64 ? ~0ull : ((1ull << hi) - 1ull));
+    for (int wl = 0; wl < hi; wl += kFD) {
+        const int width = min(kFD, hi - wl);
+        const unsigned dmask = (1u << width) - 1u;
+        if (((vary >> wl) & dmask) == 0)
+            continue;  // every key agrees on this window
+        const KeyT *ka = sk0 + a * kFinCap;
+        const int32_t *ia = si0 + a * kFinCap;
+        KeyT *kb = sk0 + (a ^ 1) * kFinCap;
+        int32_t *ib = si0 + (a ^ 1) * kFinCap;
+        // sweep 1: digit totals (lane d < 16 holds digit d)
+        uint32_t tot = 0;
+        for (int g = 0; g < ng; ++g) {
+            const int pos = g * 32 + lane;
+            const bool valid = pos < len;
+            const unsigned dig = valid ? digit_of<KeyT>(ka[pos], wl, dmask) : 0u;
+            unsigned mine = __ballot_sync(kFull, valid);
+#pragma unroll
+            for (int b = 0; b < kFD; ++b) {
+                const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
+                mine &= ((lane >> b) & 1) ? bb : ~bb;
+            }
+            tot += __popc(mine);
+        }
+        uint32_t incl = lane < kFBins ? tot : 0u;
+#pragma unroll
+        for (int o = 1; o < kFBins; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o)
+                incl += y;
+        }
+        uint32_t run = incl - (lane < kFBins ? tot : 0u);  // next free slot of digit lane
+        // sweep 2: stable scatter, group by group
+        for (int g = 0; g < ng; ++g) {
+            const int pos = g * 32 + lane;
+            const bool valid = pos < len;
+            KeyT k = 0;
+            int32_t x = 0;
+            if (valid) {
+                k = ka[pos];
+                x = ia[pos];
+            }
+            const unsigned dig = valid ? digit_of<KeyT>(k, wl, dmask) : 0u;
+            const unsigned vm = __ballot_sync(kFull, valid);
+            unsigned peers = vm, mine = vm;
+#pragma unroll
+            for (int b = 0; b < kFD; ++b) {
+                const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
+                peers &= ((dig >> b) & 1u) ? bb : ~bb;
+                mine &= ((lane >> b) & 1) ? bb : ~bb;
+            }
+            const uint32_t p = __shfl_sync(kFull, run, (int)dig) + __popc(peers & lt);
+            if (valid) {
+                kb[p] = k;
+                ib[p] = x;
+            }
+            run += __popc(mine);
+        }
+        __syncwarp();
+        a ^= 1;
+    }
+    const int32_t *ia = si0 + a * kFinCap;
+    for (int g = 0; g < ng; ++g) {
+        const int pos = g * 32 + lane;
+        if (pos < len)
+            dst[pos] = ia[pos];
+    }
+    __syncwarp();
+}
+
+// Start copying a small bucket's keys and ids into staging buffers
+// (asynchronous: they land while the previous bucket is being sorted).
+template <typename KeyT>
+__device__ __forceinline__ bool stage_bucket(const Ctx &c, const Fin &f, KeyT *pk, int32_t *pi, int lane) {
+    if (sizeof(KeyT) < 4 || f.len <= 0 || f.len > kNetMax)
+        return false;
+    const int buf = f.mode_buf & 1;
+    const KeyT *sk = reinterpret_cast<const KeyT *>(c.keyb[buf]) + f.start;
+    const int32_t *si = c.idxb[buf] + f.start;
+    for (int pos = lane; pos < f.len; pos += 32) {
+        cp_async<(int)sizeof(KeyT) < 4 ? 4 : (int)sizeof(KeyT)>(pk + pos, sk + pos);
+        cp_async<4>(pi + pos, si + pos);
+    }
+    cp_async_commit();
+    return true;
+}
+
+// One warp per bucket, buckets taken in a software pipeline: while one small
+// bucket is sorted, the next one's record is loaded and its data copied into
+// the other staging buffer.
 template <typename KeyT>
 __global__ void __launch_bounds__(32 * kFWarps) k_finish(Ctx c) {
     __shared__ __align__(16) KeyT s_key[kFWarps][2][kFinCap];
@@ -40,108 +273,54 @@ __global__ void __launch_bounds__(32 * kFWarps) k_finish(Ctx c) {
     const unsigned lt = lanemask_lt();
     const int nfin = c.ctr->fin_count;
     const int64_t gw = (int64_t)blockIdx.x * kFWarps + wid, nw = (int64_t)gridDim.x * kFWarps;
+    KeyT *sk0 = &s_key[wid][0][0];
+    int32_t *si0 = &s_idx[wid][0][0];
     long long my_elems = 0;
+    Fin f = gw < nfin ? c.fin[gw] : Fin{0, 0, 0, 0};
+    int sb = 0;  // staging buffer of f
+    bool staged = stage_bucket<KeyT>(c, f, sk0, si0, lane);
     for (int64_t e = gw; e < nfin; e += nw) {
-        const Fin f = c.fin[e];
+        const Fin fn = e + nw < nfin ? c.fin[e + nw] : Fin{0, 0, 0, 0};
         const int buf = f.mode_buf & 1;
         const int start = f.start, len = f.len;
-        if (len > kFinCap) {
-            set_status(c.status, kStOverflow);
-            continue;
-        }
-        my_elems += len;
         const int32_t *src_idx = c.idxb[buf] + start;
         const KeyT *src_key = reinterpret_cast<const KeyT *>(c.keyb[buf]) + start;
         int32_t *dst = c.F + start;
-        const int ng = (len + 31) >> 5;  // 32-element groups (warp-uniform)
-        int a = 0;                        // buffer holding the current order
-        unsigned long long a_and = ~0ull, a_or = 0ull;
-        for (int g = 0; g < ng; ++g) {
-            const int pos = g * 32 + lane;
-            if (pos < len) {
-                const KeyT k = src_key[pos];
-                s_key[wid][0][pos] = k;
-                s_idx[wid][0][pos] = src_idx[pos];
-                a_and &= (unsigned long long)k;
-                a_or |= (unsigned long long)k;
+        bool done = false;
+        if (len > kFinCap) {
+            set_status(c.status, kStOverflow);
+            done = true;
+        } else if (len <= kNetMax) {
+            my_elems += len;
+            const bool nst = stage_bucket<KeyT>(c, fn, sk0 + (sb ^ 1) * kFinCap, si0 + (sb ^ 1) * kFinCap, lane);
+            if (staged) {
+                if (nst)
+                    cp_async_wait_group1();
+                else
+                    cp_async_wait_all();
+                __syncwarp();
             }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a_and &= __shfl_xor_sync(kFull, a_and, o);
-            a_or |= __shfl_xor_sync(kFull, a_or, o);
-        }
-        __syncwarp();
-        const int hi = f.hi;
-        const unsigned long long vary = (a_and ^ a_or) & (hi >= 64 ? ~0ull : ((1ull << hi) - 1ull));
-        for (int wl = 0; wl < hi; wl += kFD) {
-            const int width = min(kFD, hi - wl);
-            const unsigned dmask = (1u << width) - 1u;
-            if (((vary >> wl) & dmask) == 0)
-                continue;  // every key agrees on this window
-            const KeyT *ka = s_key[wid][a];
-            const int32_t *ia = s_idx[wid][a];
-            KeyT *kb = s_key[wid][a ^ 1];
-            int32_t *ib = s_idx[wid][a ^ 1];
-            // sweep 1: digit totals (lane d < 16 holds digit d)
-            uint32_t tot = 0;
-            for (int g = 0; g < ng; ++g) {
-                const int pos = g * 32 + lane;
-                const bool valid = pos < len;
-                const unsigned dig = valid ? (unsigned)((unsigned long long)ka[pos] >> wl) & dmask : 0u;
-                unsigned mine = __ballot_sync(kFull, valid);
-#pragma unroll
-                for (int b = 0; b < kFD; ++b) {
-                    const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
-                    mine &= ((lane >> b) & 1) ? bb : ~bb;
-                }
-                tot += __popc(mine);
-            }
-            uint32_t incl = lane < kFBins ? tot : 0u;
-#pragma unroll
-            for (int o = 1; o < kFBins; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o)
-                    incl += y;
-            }
-            uint32_t run = incl - (lane < kFBins ? tot : 0u);  // next free slot of digit lane
-            // sweep 2: stable scatter, group by group
-            for (int g = 0; g < ng; ++g) {
-                const int pos = g * 32 + lane;
-                const bool valid = pos < len;
-                KeyT k = 0;
-                int32_t x = 0;
-                if (valid) {
-                    k = ka[pos];
-                    x = ia[pos];
-                }
-                const unsigned dig = valid ? (unsigned)((unsigned long long)k >> wl) & dmask : 0u;
-                const unsigned vm = __ballot_sync(kFull, valid);
-                unsigned peers = vm, mine = vm;
-#pragma unroll
-                for (int b = 0; b < kFD; ++b) {
-                    const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
-                    peers &= ((dig >> b) & 1u) ? bb : ~bb;
-                    mine &= ((lane >> b) & 1) ? bb : ~bb;
-                }
-                const uint32_t p = __shfl_sync(kFull, run, (int)dig) + __popc(peers & lt);
-                if (valid) {
-                    kb[p] = k;
-                    ib[p] = x;
-                }
-                run += __popc(mine);
-            }
+            done = net_finish<KeyT>(staged ? sk0 + sb * kFinCap : src_key, staged ? si0 + sb * kFinCap : src_idx,
+                                    dst, len, f.hi, lane);
             __syncwarp();
-            a ^= 1;
+            if (done) {
+                staged = nst;
+                sb ^= 1;
+            } else {
+                my_elems -= len;  // counted again below
+            }
         }
-        const int32_t *ia = s_idx[wid][a];
-        for (int g = 0; g < ng; ++g) {
-            const int pos = g * 32 + lane;
-            if (pos < len)
-                dst[pos] = ia[pos];
+        if (!done) {  // the counting path needs both buffers: nothing may be in flight into them
+            my_elems += len;
+            cp_async_wait_all();
+            __syncwarp();
+            lsd_bucket<KeyT>(src_key, src_idx, dst, len, f.hi, sk0, si0, lane, lt);
+            staged = stage_bucket<KeyT>(c, fn, sk0, si0, lane);
+            sb = 0;
         }
-        __syncwarp();
+        f = fn;
     }
+    cp_async_wait_all();  // no copy may be in flight when the warp exits
     // element count for the byte accounting (warp-uniform): one atomic per warp
     if (lane == 0 && my_elems)
         atomicAdd((unsigned long long *)&c.ctr->fin_sort_elems, (unsigned long long)my_elems);
