@@ -24,7 +24,7 @@ constexpr int kFD = 4;
 constexpr int kFBins = 1 << kFD;
 constexpr int kFWarps = 4;               // warps per finish CTA
 
-constexpr int kNetMax = 256;  // buckets up to this size are sorted by a register network
+constexpr int kNetMax = 512;  // buckets up to this size are sorted by a register network
 
 // Warp-wide bitonic sorting network over N values held in registers (lane l
 // holds the values at positions l, 32 + l, ...): stage (k, s) compares the
@@ -72,7 +72,7 @@ template <typename KeyT, int N, typename C>
 __device__ __forceinline__ void net_sort(const KeyT (&k)[N / 32], const int32_t *is, int32_t *dst, int len,
                                          int lv, int sbits, int lane) {
     constexpr int J = N / 32;
-    constexpr int PB = N == 32 ? 5 : (N == 64 ? 6 : (N == 128 ? 7 : 8));
+    constexpr int PB = N == 32 ? 5 : (N == 64 ? 6 : (N == 128 ? 7 : (N == 256 ? 8 : 9)));
     const unsigned long long smask = sbits >= 64 ? ~0ull : ((1ull << sbits) - 1ull);
     C c[J];
 #pragma unroll
@@ -93,7 +93,7 @@ template <typename KeyT, int N>
 __device__ __forceinline__ bool net_bucket(const KeyT *ks, const int32_t *is, int32_t *dst, int len, int hi,
                                            int lane) {
     constexpr int J = N / 32;
-    constexpr int PB = N == 32 ? 5 : (N == 64 ? 6 : (N == 128 ? 7 : 8));
+    constexpr int PB = N == 32 ? 5 : (N == 64 ? 6 : (N == 128 ? 7 : (N == 256 ? 8 : 9)));
     using U = typename KeyWord<KeyT>::U;
     KeyT k[J];
     U a_and = ~(U)0, a_or = 0;
@@ -127,7 +127,7 @@ __device__ __forceinline__ bool net_bucket(const KeyT *ks, const int32_t *is, in
     const int sbits = hv - lv + 1;
     if (sbits + PB <= 32)
         net_sort<KeyT, N, uint32_t>(k, is, dst, len, lv, sbits, lane);
-    else if (sbits + PB <= 64)
+    else if (N <= 256 && sbits + PB <= 64)  // (measured: at 512 nodes the counting passes win)
         net_sort<KeyT, N, unsigned long long>(k, is, dst, len, lv, sbits, lane);
     else
         return false;
@@ -143,11 +143,12 @@ __device__ __forceinline__ bool net_finish(const KeyT *ks, const int32_t *is, in
         return net_bucket<KeyT, 64>(ks, is, dst, len, hi, lane);
     if (len <= 128)
         return net_bucket<KeyT, 128>(ks, is, dst, len, hi, lane);
-    return net_bucket<KeyT, 256>(ks, is, dst, len, hi, lane);
+    if (len <= 256)
+        return net_bucket<KeyT, 256>(ks, is, dst, len, hi, lane);
+    return net_bucket<KeyT, 512>(ks, is, dst, len, hi, lane);
 }
 
-// Larger buckets (and keys whose varying bits are too wide for the network's
-// sort key) are sorted in the warp's two shared-memory buffers by counting
+// Keys whose varying bits are too wide for the network's sort key are sorted in the warp's two shared-memory buffers by counting
 // passes: every window is two sweeps over its 32-element groups, count the
 // digits (4 ballots per group), then rank each group again and scatter it to
 // the other buffer at its digit's offset.
