@@ -35,10 +35,12 @@ UNIT = "nodes/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--log2n", type=int, default=27, help="list size (27 = the benchmark workload)")
+    ap.add_argument("--key-bits", type=int, default=32,
+                    help="keys uniform over this many low bits and M = this (32 = the benchmark workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2n", type=int, default=24)
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-list batched leg")
@@ -49,11 +51,19 @@ def parse():
     return ap.parse_args()
 
 
-def workload(log2n):
+def workload(log2n, key_bits=32):
     return {"workload": f"pbit_sort_list: one 2^{log2n}-node list, SoA int32 next + uint32 key, "
-                        "seeded random list order, uniform keys, M=32, K=4",
-            "n": 1 << log2n, "key": "uint32", "layout": "SoA", "M": 32, "K": 4,
+                        f"seeded random list order, uniform keys, M={key_bits}, K=4"
+                        + ("" if key_bits == 32 else f" (keys below 2^{key_bits})"),
+            "n": 1 << log2n, "key": "uint32", "layout": "SoA", "M": key_bits, "K": 4,
             "l2": "inputs (1 GiB at 2^27) larger than L2; no flush"}
+
+
+def bench_keys(I, n, seed, key_bits):
+    key = I.uniform_keys(n, 4, seed)
+    if key_bits < 32:
+        key &= np.uint32((1 << key_bits) - 1)
+    return key
 
 
 def peaks():
@@ -79,7 +89,7 @@ class Clocks:
                 ["nvidia-smi", "-i", str(index),
                  "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -122,14 +132,14 @@ def dist():
     return ws, rank, local
 
 
-def oracle_sample(log2n, seed):
+def oracle_sample(log2n, seed, key_bits=32):
     from oracle import oracle as O
     from paper_cs_0511020_gb300 import inputs as I
     n = 1 << log2n
     nxt, root = I.random_list(n, seed)
-    key = I.uniform_keys(n, 4, seed + 1)
+    key = bench_keys(I, n, seed + 1, key_bits)
     t0 = time.perf_counter()
-    O.pbit_sort(nxt, key, root, 32, 4)
+    O.pbit_sort(nxt, key, root, key_bits, 4)
     dt = time.perf_counter() - t0
     return n, dt
 
@@ -140,10 +150,10 @@ def run_reference(a):
         return
     from oracle import oracle as O
     O.build()
-    log2n = min(22, a.log2n)
+    log2n = min(21, a.log2n)
     times = []
     for i in range(a.warmup + a.steps):
-        n, dt = oracle_sample(log2n, 0x0511020 + 2 + i)
+        n, dt = oracle_sample(log2n, 0x0511020 + 2 + i, a.key_bits)
         if i >= a.warmup:
             times.append(dt)
     tot = sum(times)
@@ -153,7 +163,7 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": workload(a.log2n),
+        "config": workload(a.log2n, a.key_bits),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
@@ -170,9 +180,12 @@ def run_ours(a):
     if world > 1:
         tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = 1 << a.log2n
+    M = a.key_bits
+    if not 4 <= M <= 32 or M % 4:
+        raise SystemExit("--key-bits must be a multiple of 4 in [4, 32]")
     seed = I.SEED_BASE + 2 + 7919 * rank
     nxt, root = I.random_list(n, seed)
-    key = I.uniform_keys(n, 4, seed + 1)
+    key = bench_keys(I, n, seed + 1, M)
     d_next0 = torch.from_numpy(nxt).cuda()
     d_next = d_next0.clone()
     d_key = torch.from_numpy(key.view(np.int32)).cuda()
@@ -182,7 +195,7 @@ def run_ours(a):
 
     def step():
         d_next.copy_(d_next0)
-        st, r = pbit.sort_pool_list(pool, root, n, 32, 4, ws=ws, stream=stream, check=False)
+        st, r = pbit.sort_pool_list(pool, root, n, M, 4, ws=ws, stream=stream, check=False)
         if st != pbit.OK:
             raise pbit.PbitError(st, "bench step")
         return r
@@ -236,7 +249,7 @@ def run_ours(a):
         h_next.copy_(h_next0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, r = pbit.sort_pool_list_host(hpool, root, n, 32, 4, ws=ws_h, stream=stream, check=False)
+        st, r = pbit.sort_pool_list_host(hpool, root, n, M, 4, ws=ws_h, stream=stream, check=False)
         dt = time.perf_counter() - t0
         if st != pbit.OK:
             raise pbit.PbitError(st, "bench e2e step")
@@ -262,7 +275,7 @@ def run_ours(a):
         achieved = s["bytes"] / (s["ms"] / 1e3) / 1e9
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"hbm_gbs of {peak_kind}",
-                "traffic": traffic_for(name, s["bytes"] / max(1, s["launches"]), a.log2n),
+                "traffic": traffic_for(name, s["launches"] / a.steps, a.log2n) if a.key_bits == 32 else None,
                 "alg_bytes_per_launch": s["bytes"] / max(1, s["launches"]),
                 "launches": s["launches"], "ms_total": s["ms"]}
     per_kernel = {k: {"ms_per_step": v["ms"] / a.steps, "GB/s": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else None,
@@ -270,21 +283,21 @@ def run_ours(a):
                   for k, v in kernel_stats.items()}
     cpu = None
     if not a.no_cpu_baseline and world == 1:
-        m, dt = oracle_sample(a.cpu_sample_log2n, 0x0511020 + 2)
+        m, dt = oracle_sample(a.cpu_sample_log2n, 0x0511020 + 2, a.key_bits)
         cpu = {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the oracle (single-threaded literal Pbit) on one 2^{a.cpu_sample_log2n}-node list "
                          f"of the same recipe ({dt:.1f} s)"}
     del d_next0, d_next, d_key, ws_h, h_next0, h_next, h_key
     torch.cuda.empty_cache()
-    batched = None if (a.no_batched or world > 1) else run_batched(a, torch, pbit, I)
+    batched = None if (a.no_batched or world > 1) else run_batched(a, torch, pbit, I, local)
     torch.cuda.empty_cache()
-    serve = None if (a.no_serve or world > 1) else run_serve(a, torch, pbit, I)
+    serve = None if (a.no_serve or world > 1) else run_serve(a, torch, pbit, I, local)
     torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
-        "config": dict(workload(a.log2n), parallelism=("replicas" if world > 1 else "single GPU"),
+        "config": dict(workload(a.log2n, a.key_bits), parallelism=("replicas" if world > 1 else "single GPU"),
                        timing="device time per step from CUDA events recorded on the launching stream "
                               "around every kernel of the call; next[] restored from a device copy before "
                               "each step, outside the timed events"),
@@ -304,7 +317,7 @@ def run_ours(a):
         tdist.destroy_process_group()
 
 
-def run_batched(a, torch, pbit, I):
+def run_batched(a, torch, pbit, I, local=0):
     """Batched workload: 4096 lists in one pool, lengths log-uniform in
     [16, 2^20], uint32 keys, random order per list, M=32.  The batch is
     autotuned, captured once as a CUDA graph and replayed; the same lists are
@@ -324,12 +337,14 @@ def run_batched(a, torch, pbit, I):
         d_next.copy_(d_next0)
         g.launch(stream)
         g.result(stream)
+    clk = Clocks(local)
     for i in range(a.steps):
         d_next.copy_(d_next0)
         e0[i].record(stream)
         g.launch(stream)
         e1[i].record(stream)
         g.result(stream)  # status of this replay (synchronizes)
+    clocks = clk.stop()
     graph_ms = [e0[i].elapsed_time(e1[i]) for i in range(a.steps)]
     gm = statistics.median(graph_ms)
 
@@ -368,13 +383,13 @@ def run_batched(a, torch, pbit, I):
            "per_list": {"value": total / fm, "unit": UNIT, "ms": 1e3 * fm,
                         "timing": "host wall clock over the whole loop of synchronous pbit_sort_list calls, "
                                   "best of 2"},
-           "speedup_vs_per_list": fm * 1e3 / gm, "same_result": same,
+           "speedup_vs_per_list": fm * 1e3 / gm, "same_result": same, "clocks": clocks,
            "autotuned": {**best, "median_ms": tune_ms}}
     g.close()
     return out
 
 
-def run_serve(a, torch, pbit, I):
+def run_serve(a, torch, pbit, I, local=0):
     """Serving workload: open-loop Poisson arrivals (mean gap 0.5 ms), lengths
     log-uniform in [2^4, 2^24], key widths 2/4/8 bytes in 1:2:1 (M = 8 x
     width), pools resident on the device, 16 GB admission budget.  Latency =
@@ -399,6 +414,7 @@ def run_serve(a, torch, pbit, I):
                 "mean_ms": float(lat.mean()), "value": nodes / ((t_last - t_first) / 1e9), "unit": UNIT}
 
     srv = pbit.Server(mem_budget_bytes=16 << 30, streams=4, max_batch=64)
+    clk = Clocks(local)
     tickets = []
     t0 = time.monotonic_ns() + 20_000_000
     sched = [t0 + int(x * 1e9) for x in arr]
@@ -413,6 +429,7 @@ def run_serve(a, torch, pbit, I):
             raise pbit.PbitError(st, "served request")
         done.append(srv.times(t)[1])
     stats = srv.stats()
+    clocks = clk.stop()
     srv.close()
     W = a.serve_warmup
     lat = [done[i] - sched[i] for i in range(R)]
@@ -442,15 +459,16 @@ def run_serve(a, torch, pbit, I):
                         "16 GB admission budget, 4 streams, batches of up to 64",
             "requests": a.serve_requests, "warmup_requests": W, "offered_nodes_per_s": offered,
             "served": {**served, "batches": stats["batches"], "max_batch": stats["max_batch"],
-                       "peak_admitted_bytes": stats["peak_bytes"]},
+                       "peak_admitted_bytes": stats["peak_bytes"], "clocks": clocks},
             "fifo_per_list": fifo,
             "latency": "completion seen by the scheduler (served) or after the synchronous call returns "
                        "(FIFO) minus the scheduled arrival, host monotonic clock"}
 
 
-def traffic_for(name, alg_bytes, log2n):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current source of that kernel; else None."""
+def traffic_for(name, launches_per_step, log2n):
+    """DRAM bytes per launch from the committed ncu capture (profiles/traffic.json:
+    the kernel kind's DRAM bytes in one sort), if it was taken on the current
+    source of that kernel and on this list size; else None."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -466,7 +484,9 @@ def traffic_for(name, alg_bytes, log2n):
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
-    return e["dram_bytes_per_launch"] if h == e.get("source_sha") else None
+    if h != e.get("source_sha") or not launches_per_step:
+        return None
+    return e["dram_bytes_total"] / launches_per_step
 
 
 if __name__ == "__main__":
