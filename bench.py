@@ -125,6 +125,20 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def whole_job_rate(units_per_rank, seconds, world, device):
+    """Whole-job throughput: all ranks' units over the slowest rank's time
+    (max over ranks; every rank does the same amount of work).  Returns
+    (rate, max seconds).  Collective only when world > 1."""
+    t = float(seconds)
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        tdist.all_reduce(x, op=tdist.ReduceOp.MAX)
+        t = float(x.item())
+    return world * units_per_rank / t, t
+
+
 def dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,12 +243,8 @@ def run_ours(a):
     clocks = clk.stop()
     pbit.profile_enable(False)
     launches_per_step = pbit.last_launch_count()
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * a.steps * n / (tot_ms / 1e3)
+    value, tot_s = whole_job_rate(a.steps * n, sum(step_ms) / 1e3, world, "cuda")
+    tot_ms = tot_s * 1e3
 
     # ---- end to end through the host-buffer C ABI call (pinned host memory)
     h_next0 = torch.from_numpy(nxt).pin_memory()
@@ -255,12 +265,7 @@ def run_ours(a):
             raise pbit.PbitError(st, "bench e2e step")
         if i >= a.warmup:
             e2e_times.append(dt)
-    e2e_tot = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_tot], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = world * a.steps * n / e2e_tot
+    e2e_value, _ = whole_job_rate(a.steps * n, sum(e2e_times), world, "cuda")
 
     if rank != 0:
         if world > 1:
