@@ -144,6 +144,7 @@ Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms) {
     const int64_t iters = (8 * kb + t.digit_bits - 1) / t.digit_bits;
     z.fin_cap = L + (int64_t)(1 << t.digit_bits) * iters * z.seg_cap + 16;
     z.tile_cap = ncap / pass_tile() + z.seg_cap + 2;
+    z.mid_cap = ncap / (t.cutoff + 1) + L + 16;  // disjoint buckets of more than cutoff nodes
     // A random gather costs a whole DRAM sector or more: the pack turns the
     // walk's two gathers per hop into one.
     z.pack = t.pack == 2 || (t.pack == 0 && ncap * (4 + kb) > kPackAutoBytes);
@@ -176,6 +177,7 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     x.chunk_cap = z.chunk_cap;
     x.seg_cap = z.seg_cap;
     x.fin_cap = z.fin_cap;
+    x.mid_cap = z.mid_cap;
     x.tile_cap = z.tile_cap;
     const int bins = 1 << z.tune.digit_bits;
 
@@ -229,7 +231,9 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     }
     x.ctot = (uint32_t *)take(4 * (size_t)x.scan_cap * bins);
     x.plan_cnt = (int4 *)take(sizeof(int4) * (size_t)z.seg_cap);
+    x.plan_mid = (int32_t *)take(4 * (size_t)z.seg_cap);
     x.fin = (Fin *)take(sizeof(Fin) * (size_t)z.fin_cap);
+    x.mid = (Fin *)take(sizeof(Fin) * (size_t)z.mid_cap);
     x.lb = (unsigned long long *)take(8 * (size_t)z.tile_cap * bins);
     zero(x.lb, 0, 8 * (size_t)z.tile_cap * bins);
     x.rel_cursor = (int32_t *)take(4 * (size_t)relink_max_buckets());

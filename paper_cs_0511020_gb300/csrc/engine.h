@@ -25,7 +25,7 @@ struct Sizes {
     int kb;
     Tune tune;
     int CH;
-    int64_t R0, Rcap, chunk_cap, seg_cap, fin_cap, tile_cap;
+    int64_t R0, Rcap, chunk_cap, seg_cap, fin_cap, tile_cap, mid_cap;
     bool pack;
 };
 

@@ -124,6 +124,12 @@ __device__ void block_excl_scan16(uint32_t (&v)[kBins], uint32_t (&tot)[kBins], 
 }
 
 __device__ __forceinline__ int top_bit(unsigned long long v) { return 63 - __clzll((long long)v); }
+
+// A bucket of more than the cutoff goes to the CTA finish when it fits its
+// shared memory and at most kMidSpan of its key bits vary (v: varying bits).
+__device__ __forceinline__ bool mid_bucket(int len, unsigned long long v) {
+    return len <= kMidCap && (v == 0 || top_bit(v) - (__ffsll((long long)v) - 1) < kMidSpan);
+}
 __device__ __forceinline__ unsigned long long low_mask(int bits) {
     return bits >= 64 ? ~0ull : ((1ull << bits) - 1ull);
 }
@@ -133,13 +139,14 @@ __device__ __forceinline__ unsigned long long low_mask(int bits) {
 // cutoff go straight to the shared-memory finish, the rest are pending.
 __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
     __shared__ int sh[40];
-    __shared__ int s_fin_base, s_pend_base, s_tile_base;
+    __shared__ int s_fin_base, s_pend_base, s_tile_base, s_mid_base;
     if (*(volatile int32_t *)c.status)
         return;
     if (threadIdx.x == 0) {
         s_fin_base = 0;
         s_pend_base = 0;
         s_tile_base = 0;
+        s_mid_base = 0;
     }
     __syncthreads();
     const int L = c.num_lists;
@@ -151,12 +158,23 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
             start = c.desc[i].out_base;
         }
         int is_fin = (i < L && n >= 1 && n <= c.cutoff) ? 1 : 0;
-        int is_pend = (i < L && n > c.cutoff) ? 1 : 0;
+        // (a list's varying bits are not known yet: only M bits few enough
+        // for the CTA finish qualify it directly; others go through seg_stats)
+        int is_mid = (i < L && n > c.cutoff && n <= kMidCap && c.M <= kMidSpan) ? 1 : 0;
+        int is_pend = (i < L && n > c.cutoff && !is_mid) ? 1 : 0;
         int tiles = is_pend ? tiles_of(n, kTile) : 0;
-        int tf, tp, tt;
+        int tf, tp, tt, tm;
         int pf = block_excl_scan(is_fin, &tf, sh);
         int pp = block_excl_scan(is_pend, &tp, sh);
         int pt = block_excl_scan(tiles, &tt, sh);
+        int pm = block_excl_scan(is_mid, &tm, sh);
+        if (is_mid) {
+            int k = s_mid_base + pm;
+            if (k < c.mid_cap)
+                c.mid[k] = Fin{start, n, c.M, (1 << 8) | 0};
+            else
+                set_status(c.status, kStOverflow);
+        }
         if (is_fin) {
             int k = s_fin_base + pf;
             if (k < c.fin_cap)
@@ -178,11 +196,13 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
             s_fin_base += tf;
             s_pend_base += tp;
             s_tile_base += tt;
+            s_mid_base += tm;
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         c.ctr->fin_count = s_fin_base;
+        c.ctr->mid_count = (int32_t)min((int64_t)s_mid_base, c.mid_cap);
         c.ctr->pend_count[0] = (int32_t)min((int64_t)s_pend_base, c.seg_cap);
         if (s_pend_base < c.seg_cap)
             c.pend_tile_base[0][s_pend_base] = s_tile_base;
@@ -316,7 +336,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
         s_nrow_base = 0;
     }
     __syncthreads();
-    int fin_total = 0;
+    int fin_total = 0, mid_total = 0;
     for (int r0 = 0; r0 < P; r0 += blockDim.x) {
         const int s = r0 + threadIdx.x;
         int kind = 0;  // 1 small (no varying bit), 2 small, 3 active, 4 pending again, 5 active final
@@ -334,6 +354,8 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
                 else
                     kind = (t >= sg.hi - kD) ? 3 : 4;
             }
+            if (kind >= 3 && mid_bucket(sg.len, v))
+                kind = 6;  // one CTA finishes it
         }
         const int tiles = kind == 4 ? tiles_of(sg.len, kTile) : 0;
         int tf, ta, tr, tt;
@@ -341,7 +363,15 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
         const int pa = block_excl_scan(kind == 3 || kind == 5, &ta, sh);
         const int pr = block_excl_scan(kind == 4, &tr, sh);
         const int pt = block_excl_scan(tiles, &tt, sh);
-        if (kind == 1 || kind == 2) {
+        int tm;
+        const int pm = block_excl_scan(kind == 6, &tm, sh);
+        if (kind == 6) {
+            const int64_t k = (int64_t)c.ctr->mid_count + mid_total + pm;
+            if (k < c.mid_cap)
+                c.mid[k] = Fin{sg.start, sg.len, sg.hi, (1 << 8) | (sg.buf & 1)};
+            else
+                set_status(c.status, kStOverflow);
+        } else if (kind == 1 || kind == 2) {
             const int64_t k = (int64_t)c.ctr->fin_count + fin_total + pf;
             if (k < c.fin_cap)
                 c.fin[k] = Fin{sg.start, sg.len, kind == 2 ? t + 1 : 0, ((kind == 2 ? 1 : 0) << 8) | (sg.buf & 1)};
@@ -368,6 +398,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
             c.por[cur][s] = 0ull;
         }
         fin_total += tf;
+        mid_total += tm;
         __syncthreads();
         if (threadIdx.x == 0) {
             s_act_base += ta;
@@ -378,6 +409,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
     }
     if (threadIdx.x == 0) {
         c.ctr->fin_count += fin_total;
+        c.ctr->mid_count = (int32_t)min((int64_t)c.ctr->mid_count + mid_total, c.mid_cap);
         c.ctr->act_count[cur] = (int32_t)min((int64_t)s_act_base, c.seg_cap);
         c.ctr->pend_count[nxt] = (int32_t)min((int64_t)s_re_base, c.seg_cap);
         c.ctr->stat_tiles[nxt] = s_re_tiles;
@@ -848,13 +880,16 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
 
 // ------------------------------------------------------------------ plan
 // kinds: 0 none, 1 small (no varying bit), 2 small, 3 next active, 4 pending,
-// 5 next active final (all keys equal; written straight to F by the pass)
+// 5 next active final (all keys equal; written straight to F by the pass),
+// 6 mid-size (finished by one CTA in shared memory)
 __device__ __forceinline__ int classify_bucket(const Ctx &c, int cur, int s, const Seg &sg, int d,
                                                uint32_t cnt, int *t_out) {
     if (cnt == 0 || sg.lo == 0 || sg.final)
         return 0;
     const int64_t r = (int64_t)s * kBins + d;
     const unsigned long long v = (c.bor[cur][r] ^ c.band[cur][r]) & low_mask(sg.lo);
+    if ((int)cnt > c.cutoff && mid_bucket((int)cnt, v))
+        return 6;  // one CTA finishes it
     if (cnt == 1 || v == 0)
         return (int)cnt <= c.cutoff ? 1 : 5;
     const int t = top_bit(v);
@@ -873,7 +908,7 @@ __global__ void k_plan_count(Ctx c, int it) {
     const int A = c.ctr->act_count[cur];
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A; s += gridDim.x * blockDim.x) {
         const Seg sg = c.act[cur][s];
-        int na = 0, np = 0, nf = 0, nt = 0;
+        int na = 0, np = 0, nf = 0, nt = 0, nm = 0;
         const uint32_t *h = c.act_hist[cur] + (int64_t)s * kBins;
         for (int d = 0; d < kBins; ++d) {
             int t = 0;
@@ -883,15 +918,17 @@ __global__ void k_plan_count(Ctx c, int it) {
             np += kd == 4;
             nf += (kd == 1 || kd == 2);
             nt += (kd == 4) ? tiles_of(cnt, kTile) : 0;
+            nm += kd == 6;
         }
         c.plan_cnt[s] = make_int4(na, np, nf, nt);
+        c.plan_mid[s] = nm;
     }
 }
 
 // exclusive scan of the per-segment counts (one CTA), new counters
 __global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
     __shared__ int sh[40];
-    __shared__ int s_a, s_p, s_f, s_t;
+    __shared__ int s_a, s_p, s_f, s_t, s_m;
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1, nxt = cur ^ 1;
@@ -901,20 +938,24 @@ __global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
         s_p = c.ctr->pend_count[nxt];  // after the segments plan_pending re-queued
         s_f = c.ctr->fin_count;
         s_t = c.ctr->stat_tiles[nxt];
+        s_m = c.ctr->mid_count;
     }
     __syncthreads();
     constexpr int kPer = 8;
     for (int r0 = 0; r0 < A; r0 += blockDim.x * kPer) {
         const int s0 = r0 + threadIdx.x * kPer;
         int4 sum = make_int4(0, 0, 0, 0);
+        int msum = 0;
         for (int u = 0; u < kPer && s0 + u < A; ++u) {
             const int4 v = c.plan_cnt[s0 + u];
             sum.x += v.x;
             sum.y += v.y;
             sum.z += v.z;
             sum.w += v.w;
+            msum += c.plan_mid[s0 + u];
         }
-        int ta, tp, tf, tt;
+        int ta, tp, tf, tt, tm;
+        int pm = block_excl_scan(msum, &tm, sh);
         int pa = block_excl_scan(sum.x, &ta, sh);
         int pp = block_excl_scan(sum.y, &tp, sh);
         int pf = block_excl_scan(sum.z, &tf, sh);
@@ -922,6 +963,9 @@ __global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
         for (int u = 0; u < kPer && s0 + u < A; ++u) {
             const int4 v = c.plan_cnt[s0 + u];
             c.plan_cnt[s0 + u] = make_int4(s_a + pa, s_p + pp, s_f + pf, s_t + pt);
+            const int vm = c.plan_mid[s0 + u];
+            c.plan_mid[s0 + u] = s_m + pm;
+            pm += vm;
             pa += v.x;
             pp += v.y;
             pf += v.z;
@@ -933,12 +977,15 @@ __global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
             s_p += tp;
             s_f += tf;
             s_t += tt;
+            s_m += tm;
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        if (s_a > c.seg_cap || s_p > c.seg_cap || s_f > c.fin_cap || c.ctr->brows[nxt] + s_t > c.row_cap)
+        if (s_a > c.seg_cap || s_p > c.seg_cap || s_f > c.fin_cap || c.ctr->brows[nxt] + s_t > c.row_cap ||
+            s_m > c.mid_cap)
             set_status(c.status, kStOverflow);
+        c.ctr->mid_count = (int32_t)min((int64_t)s_m, c.mid_cap);
         c.ctr->act_count[nxt] = (int32_t)min((int64_t)s_a, c.seg_cap);
         c.ctr->pend_count[nxt] = (int32_t)min((int64_t)s_p, c.seg_cap);
         if (s_p <= c.seg_cap)
@@ -956,7 +1003,7 @@ __global__ void k_plan_write(Ctx c, int it) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A; s += gridDim.x * blockDim.x) {
         const Seg sg = c.act[cur][s];
         const int4 o = c.plan_cnt[s];
-        int64_t a = o.x, p = o.y, f = o.z, tb = o.w;
+        int64_t a = o.x, p = o.y, f = o.z, tb = o.w, m = c.plan_mid[s];
         const uint32_t *h = c.act_hist[cur] + (int64_t)s * kBins;
         int32_t bstart = sg.start;
         int32_t nrow = c.act_nrow_base[cur][s];
@@ -964,7 +1011,11 @@ __global__ void k_plan_write(Ctx c, int it) {
             int t = 0;
             const uint32_t cnt = h[d];
             const int kd = classify_bucket(c, cur, s, sg, d, cnt, &t);
-            if (kd == 1 || kd == 2) {
+            if (kd == 6) {
+                if (m < c.mid_cap)
+                    c.mid[m] = Fin{bstart, (int32_t)cnt, sg.lo, (1 << 8) | ((sg.buf & 1) ^ 1)};
+                ++m;
+            } else if (kd == 1 || kd == 2) {
                 if (f < c.fin_cap)
                     c.fin[f] = Fin{bstart, (int32_t)cnt, kd == 2 ? t + 1 : 0,
                                    ((kd == 2 ? 1 : 0) << 8) | ((sg.buf & 1) ^ 1)};

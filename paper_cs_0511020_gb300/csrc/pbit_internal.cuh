@@ -56,6 +56,10 @@ struct Fin {
 };
 
 constexpr int kMaxIters = 64;
+// Buckets of (cutoff, kMidCap] nodes are finished by one CTA each in shared
+// memory instead of going through further global passes.
+constexpr int kMidCap = 4096;
+constexpr int kMidSpan = 16;  // ... when at most this many of their key bits vary (4 windows)
 
 // Work counters that many CTAs hit at once sit on their own 128-byte lines
 // (an atomic on a line is serialized in one L2 slice).
@@ -70,6 +74,7 @@ struct Counters {
     HotCounter fin_ctr;        // work counter of the finish kernel
     int32_t n_virt;            // total nodes over all lists
     int32_t fin_count;
+    int32_t mid_count;         // buckets finished by one CTA each
     int32_t act_count[2];
     int32_t pend_count[2];
     int32_t num_tiles[2];
@@ -145,7 +150,10 @@ struct Ctx {
     unsigned long long *pand[2];
     unsigned long long *por[2];
     int4 *plan_cnt;             // seg_cap per-segment counts -> offsets
+    int32_t *plan_mid;          // seg_cap per-segment mid-bucket counts -> offsets
     Fin *fin;
+    Fin *mid;                   // mid_cap buckets of (cutoff, kMidCap] nodes: one CTA each
+    int64_t mid_cap;
     unsigned long long *lb;     // tile_cap x 16 look-back words
     int32_t *rel_cursor;        // blocked relink: pairs per node block
     int32_t *new_roots;

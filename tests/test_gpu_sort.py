@@ -297,3 +297,61 @@ def test_gather_pack_on_and_off(pb, case, pack):
         return
     kb = {"u8": 1, "u16": 2, "u32": 4, "u64": 8}[case]
     _check_vs_oracle(pb, nxt, I.uniform_keys(n, kb, 175 + kb), root, 8 * kb, tune=tune)
+
+
+@pytest.mark.parametrize("pattern", ["split", "big_sub_bucket", "wide_span", "narrow_span", "u16_direct",
+                                     "u8_direct", "u64_mid", "equal_top"])
+@pytest.mark.parametrize("n", [600, 2049, 4096])
+def test_mid_size_buckets(pb, pattern, n):
+    """Buckets of 513..4096 nodes whose keys vary in at most 16 bits are
+    finished by one CTA: one split on the top 4 varying bits then register
+    networks per sub-bucket, or least-significant windows over the whole
+    span when a sub-bucket would exceed 512 nodes or its network key 32
+    bits."""
+    g = I.rng(200 + n + len(pattern))
+    nxt, root = I.random_list(n, 201 + n)
+    M = 32
+    if pattern == "split":            # 12 varying bits: split + networks
+        key = g.integers(0, 1 << 12, n, dtype=np.uint32)
+    elif pattern == "big_sub_bucket":  # 70% share their top varying bits: LSD fallback
+        key = g.integers(0, 1 << 14, n, dtype=np.uint32)
+        key[g.random(n) < 0.7] &= np.uint32(0x3FF)
+    elif pattern == "wide_span":       # bits 16..31 vary: network key too wide, LSD windows
+        key = g.integers(0, 1 << 16, n, dtype=np.uint32) << np.uint32(16)
+    elif pattern == "narrow_span":     # 3 varying bits: one window
+        key = (g.integers(0, 8, n, dtype=np.uint32) << np.uint32(9)) | np.uint32(0x40000001)
+    elif pattern == "u16_direct":      # M = 16: the list itself goes to the CTA finish
+        key = I.uniform_keys(n, 2, 202 + n)
+        M = 16
+    elif pattern == "u8_direct":
+        key = I.uniform_keys(n, 1, 203 + n)
+        M = 8
+    elif pattern == "u64_mid":         # 64-bit keys, 16 varying bits in the middle
+        key = (g.integers(0, 1 << 16, n, dtype=np.uint64) << np.uint64(20)) | np.uint64(0x5 << 60)
+        M = 64
+    else:                              # all keys equal in the varying window's top, ties in list order
+        key = np.full(n, 0x1234, np.uint32)
+        key[::5] = 0x1235
+    if (M // 4) % 2 == 0:
+        _check_vs_oracle(pb, nxt, key, root, M)
+    else:
+        st, got, r = _gpu_sort(pb, nxt, key, root, M)
+        want, wr = O.stable_sort_definition(nxt, key, root, M)
+        assert st == pb.OK and r == wr and (got == want).all()
+
+
+def test_mid_size_buckets_batched(pb):
+    """Many mid-size lists in one batch (the CTA finish takes them from the
+    initial plan) next to small and large ones."""
+    lens = np.array([513, 4096, 700, 12, 5000, 1, 3000, 4097, 2048, 520] * 6, dtype=np.int64)
+    nxt, key, roots, off = I.batched_pool(lens, 2, 210)
+    d_next = torch.from_numpy(nxt.copy()).cuda()
+    nr = pb.sort_lists_batched(d_next, _dev_key(key), torch.from_numpy(roots).cuda(),
+                               torch.from_numpy(off).cuda(), M=16, K=4)
+    got, nr = d_next.cpu().numpy(), nr.cpu().numpy()
+    for i in range(lens.size):
+        a, b = off[i], off[i + 1]
+        sub_next = np.where(nxt[a:b] >= 0, nxt[a:b] - a, -1).astype(np.int32)
+        want, wr, _ = O.pbit_sort(sub_next, key[a:b], roots[i] - a, 16, 4)
+        assert nr[i] == wr + a
+        assert (got[a:b] == np.where(want >= 0, want + a, -1)).all(), f"list {i}"
