@@ -32,7 +32,7 @@ struct ProfState {
     cudaEvent_t start = nullptr;
     Counters ctr;
     bool have_ctr = false;
-    int64_t n = 0, rcap = 0, rounds = 0;
+    int64_t n = 0, rcap = 0, scap = 0, rounds = 0;
     int kb = 4;
     bool blocked_relink = false;
     bool pack = false;
@@ -196,6 +196,9 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     zero(x.task_succ, 0xff, 4 * (size_t)z.Rcap);
     for (int b = 0; b < 2; ++b)
         x.wy[b] = (int64_t *)take(8 * (size_t)z.Rcap);
+    x.Scap = (int32_t)((z.Rcap + 31) / 32 + 1 + z.L);  // grid walks, one gap, root walks
+    for (int b = 0; b < 2; ++b)
+        x.sw[b] = (int64_t *)take(8 * (size_t)x.Scap);
     x.chunk_task = (int32_t *)take(4 * (size_t)z.chunk_cap);
     zero(x.chunk_task, 0xff, 4 * (size_t)z.chunk_cap);
     x.chunk_j0 = (int32_t *)take(4 * (size_t)z.chunk_cap);
@@ -271,11 +274,11 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     if (cc.pack)
         ++n;
     launch_walk(cc, s, sms);
-    const int rounds = ceil_log2(cc.Rcap) + 1;
+    const int rounds = ceil_log2(cc.Scap) + 1;  // pointer jumping over the ruler walks
     launch_wyllie(cc, s, sms, rounds);
-    launch_validate_emit(cc, rounds & 1, s, sms);
+    launch_validate_emit(cc, s, sms);
     launch_plan_init(cc, s);
-    n += 7 + rounds;
+    n += 8 + rounds;
     const int iters = (M + cc.D - 1) / cc.D;
     for (int it = 0; it < iters; ++it)
         launch_iteration(cc, it, s, sms);
@@ -285,6 +288,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     n += 4;
     if (g_prof.on) {
         g_prof.rcap = cc.Rcap;
+        g_prof.scap = cc.Scap;
         g_prof.rounds = rounds;
         g_prof.kb = cc.key_bytes;
         g_prof.blocked_relink = relink_blocked(cc);
@@ -557,7 +561,9 @@ int32_t pbit_profile_read(pbit_kernel_stat *out, int32_t max) {
             } else if (!std::strcmp(nm, "emit")) {
                 b = n * 2.0 * (4.0 + kb);
             } else if (!std::strcmp(nm, "wyllie")) {
-                b = (double)g_prof.rcap * (16.0 + 24.0 * (double)g_prof.rounds);
+                // ruler walks: read len + succ, write (walk, prefix) per ruler;
+                // pointer jumping over the walks; expand: read both, write one
+                b = (double)g_prof.rcap * (16.0 + 24.0) + (double)g_prof.scap * 24.0 * (double)g_prof.rounds;
             } else if (!std::strcmp(nm, "seg_stats")) {
                 for (int it = 0; it < kMaxIters; ++it)
                     b += (double)k.stat_elems[it] * kb;

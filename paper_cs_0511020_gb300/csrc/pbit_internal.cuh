@@ -121,7 +121,10 @@ struct Ctx {
     int32_t *task_list;
     int32_t *task_len;
     int32_t *task_succ;
-    int64_t *wy[2];     // packed (succ << 32) | suffix length, ping-pong
+    int64_t *wy[2];     // wy[0]: per task (succ << 32) | suffix length; wy[1]: per task
+                        // (walk << 32) | nodes before it in its walk
+    int64_t *sw[2];     // per ruler walk: (succ walk << 32) | nodes, pointer-jumping ping-pong
+    int32_t Scap;       // ruler walks: ceil(Rcap / 32) + 1 + num_lists
     int32_t *chunk_task;
     int32_t *chunk_j0;
     int32_t *chunk_data;        // chunk_cap x CH node ids (virtual positions)
@@ -349,7 +352,7 @@ void launch_setup(const Ctx &c, const int64_t *d_offsets, const int32_t *d_roots
 void launch_pack(const Ctx &c, cudaStream_t s, int sms);
 void launch_walk(const Ctx &c, cudaStream_t s, int sms);
 void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds);
-void launch_validate_emit(const Ctx &c, int final_wy, cudaStream_t s, int sms);
+void launch_validate_emit(const Ctx &c, cudaStream_t s, int sms);
 void launch_plan_init(const Ctx &c, cudaStream_t s);
 void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms);
 void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms);

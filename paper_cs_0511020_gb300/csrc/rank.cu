@@ -8,7 +8,8 @@
 //   walk      every ruler walks next[] to the next ruler, writing the nodes it
 //             visits and their sort keys into chunks (one dependent gather of
 //             next[] and one independent gather of key[] per hop)
-//   wyllie    pointer jumping over the ruler sublists -> offset of each sublist
+//   wyllie    walks over the ruler chain from every 32nd ruler, pointer
+//             jumping over those walks -> offset of each sublist
 //   validate  the root's ruler chain must end at NULL after exactly n nodes
 //   emit      chunks -> (ord_idx, ord_key) at their ranks
 #include "pbit_internal.cuh"
@@ -365,37 +366,95 @@ __global__ void __launch_bounds__(256, 6) k_walk(Ctx c) {
 }
 
 // ----------------------------------------------------------------- wyllie
-__global__ void k_wy_init(Ctx c) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < c.Rcap;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int32_t s = c.task_succ[t];
-        uint32_t l = (uint32_t)c.task_len[t];
-        c.wy[0][t] = (int64_t)(((uint64_t)(uint32_t)s << 32) | l);
+// Ranking the rulers in two levels.  Every 32nd ruler task (and the task of
+// every list's root) walks the ruler chain (task_succ) to the next such
+// task, recording for each task it passes its walk and the number of nodes
+// before it in the walk; a valid list never leads back into a root's task,
+// so walks need not recognise roots.  Pointer jumping (Wyllie) then runs
+// over the walks only, ~32 times fewer than the rulers, and every task's
+// suffix length = its walk's suffix length - the nodes before it.
+__device__ __forceinline__ int64_t wy_pack(int32_t succ, uint32_t v) {
+    return (int64_t)(((uint64_t)(uint32_t)succ << 32) | v);
+}
+
+__global__ void k_ruler_walk(Ctx c) {
+    const int32_t nreg = (c.Rcap + 31) / 32;  // walks started at tasks 0, 32, 64, ...
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < c.Scap;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        int32_t t = -1;
+        if (w < nreg) {
+            t = (int32_t)w * 32;
+        } else if (w > nreg && w - nreg - 1 < c.num_lists) {
+            const int32_t rt = c.root_task[w - nreg - 1];
+            if (rt >= 0 && (rt & 31) != 0)
+                t = rt;  // a root task off the 32-grid starts its own walk
+        }
+        if (t < 0 || t >= c.Rcap || c.task_len[t] <= 0) {
+            c.sw[0][w] = wy_pack(-1, 0);  // no walk here
+            continue;
+        }
+        uint32_t before = 0;
+        int32_t u = t, succ = -1;
+        for (int32_t hops = 0; hops <= c.Rcap; ++hops) {
+            c.wy[1][u] = wy_pack((int32_t)w, before);
+            before += (uint32_t)c.task_len[u];
+            const int32_t v = c.task_succ[u];
+            if (v < 0)
+                break;
+            if (v >= c.Rcap) {
+                set_status(c.status, PBIT_EBADLIST);
+                break;
+            }
+            if ((v & 31) == 0) {
+                succ = v >> 5;
+                break;
+            }
+            u = v;
+            if (hops == c.Rcap)
+                set_status(c.status, PBIT_EBADLIST);  // a cycle off the grid
+        }
+        c.sw[0][w] = wy_pack(succ, before);
     }
 }
 
-// One pointer-jumping round: (s, v) <- (succ(s), v + v(s)).
-__global__ void k_wy_round(Ctx c, int in) {
-    const int64_t *a = c.wy[in];
-    int64_t *b = c.wy[in ^ 1];
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < c.Rcap;
-         t += (int64_t)gridDim.x * blockDim.x) {
+// One pointer-jumping round over the walks: (s, v) <- (succ(s), v + v(s)).
+__global__ void k_wy_round(const int64_t *a, int64_t *b, int32_t n) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t x = (uint64_t)a[t];
-        int32_t s = (int32_t)(x >> 32);
+        const int32_t s = (int32_t)(x >> 32);
         if (s >= 0) {
-            uint64_t y = (uint64_t)a[s];
-            uint32_t val = (uint32_t)x + (uint32_t)y;
+            const uint64_t y = (uint64_t)a[s];
+            const uint32_t val = (uint32_t)x + (uint32_t)y;
             x = (y & 0xffffffff00000000ull) | val;
         }
         b[t] = (int64_t)x;
     }
 }
 
+// Every task: (end of its chain, suffix length) from its walk's.  A task no
+// walk reached (only in a malformed list) gets succ -2.
+__global__ void k_ruler_expand(Ctx c, int fin) {
+    const int64_t *sw = c.sw[fin];
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < c.Rcap;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (c.task_len[t] <= 0)
+            continue;
+        const uint64_t m = (uint64_t)c.wy[1][t];
+        const int32_t w = (int32_t)(m >> 32);
+        if (w < 0 || w >= c.Scap) {
+            c.wy[0][t] = wy_pack(-2, 0);
+            continue;
+        }
+        const uint64_t s = (uint64_t)sw[w];
+        c.wy[0][t] = wy_pack((int32_t)(s >> 32), (uint32_t)s - (uint32_t)m);
+    }
+}
+
 // --------------------------------------------------------- validate + emit
-__global__ void k_validate(Ctx c, int fin) {
+__global__ void k_validate(Ctx c) {
     if (*(volatile int32_t *)c.status)
         return;
-    const int64_t *w = c.wy[fin];
+    const int64_t *w = c.wy[0];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.num_lists; i += gridDim.x * blockDim.x) {
         const ListDesc &d = c.desc[i];
         int32_t rt = c.root_task[i];
@@ -416,14 +475,14 @@ __global__ void k_validate(Ctx c, int fin) {
 // metadata loads of 32 chunks overlap; then the chunks are copied four at a
 // time with all loads issued before the stores.
 template <typename KeyT>
-__global__ void __launch_bounds__(256) k_emit(Ctx c, int fin) {
+__global__ void __launch_bounds__(256) k_emit(Ctx c) {
     if (*(volatile int32_t *)c.status)
         return;
     const int lane = threadIdx.x & 31;
     const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nchunks = min((int64_t)c.ctr->chunk_next.v, c.chunk_cap);
-    const int64_t *w = c.wy[fin];
+    const int64_t *w = c.wy[0];
     const KeyT *ckey = reinterpret_cast<const KeyT *>(c.chunk_key);
     KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[0]);
     int32_t *oidx = c.idxb[0];
@@ -515,24 +574,28 @@ void launch_walk(const Ctx &c, cudaStream_t s, int sms) {
 }
 
 void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds) {
-    int64_t blocks = min((int64_t)sms * 8, max((int64_t)1, ((int64_t)c.Rcap + 255) / 256));
-    k_wy_init<<<(unsigned)blocks, 256, 0, s>>>(c);
+    const int64_t wb = min((int64_t)sms * 8, max((int64_t)1, ((int64_t)c.Scap + 127) / 128));
+    k_ruler_walk<<<(unsigned)wb, 128, 0, s>>>(c);
     prof_mark("wyllie", s);
+    const int64_t rb = min((int64_t)sms * 8, max((int64_t)1, ((int64_t)c.Scap + 255) / 256));
     for (int r = 0; r < rounds; ++r) {
-        k_wy_round<<<(unsigned)blocks, 256, 0, s>>>(c, r & 1);
+        k_wy_round<<<(unsigned)rb, 256, 0, s>>>(c.sw[r & 1], c.sw[(r & 1) ^ 1], c.Scap);
         prof_mark("wyllie", s);
     }
+    const int64_t eb = min((int64_t)sms * 8, max((int64_t)1, ((int64_t)c.Rcap + 255) / 256));
+    k_ruler_expand<<<(unsigned)eb, 256, 0, s>>>(c, rounds & 1);
+    prof_mark("wyllie", s);
 }
 
-void launch_validate_emit(const Ctx &c, int fin, cudaStream_t s, int sms) {
-    k_validate<<<max(1, min(sms, (c.num_lists + 255) / 256)), 256, 0, s>>>(c, fin);
+void launch_validate_emit(const Ctx &c, cudaStream_t s, int sms) {
+    k_validate<<<max(1, min(sms, (c.num_lists + 255) / 256)), 256, 0, s>>>(c);
     prof_mark("validate", s);
     unsigned blocks = (unsigned)(sms * 8);
     switch (c.key_bytes) {
-    case 1: k_emit<uint8_t><<<blocks, 256, 0, s>>>(c, fin); break;
-    case 2: k_emit<uint16_t><<<blocks, 256, 0, s>>>(c, fin); break;
-    case 4: k_emit<uint32_t><<<blocks, 256, 0, s>>>(c, fin); break;
-    default: k_emit<unsigned long long><<<blocks, 256, 0, s>>>(c, fin); break;
+    case 1: k_emit<uint8_t><<<blocks, 256, 0, s>>>(c); break;
+    case 2: k_emit<uint16_t><<<blocks, 256, 0, s>>>(c); break;
+    case 4: k_emit<uint32_t><<<blocks, 256, 0, s>>>(c); break;
+    default: k_emit<unsigned long long><<<blocks, 256, 0, s>>>(c); break;
     }
     prof_mark("emit", s);
 }
