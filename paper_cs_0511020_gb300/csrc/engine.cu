@@ -36,6 +36,7 @@ struct ProfState {
     int kb = 4;
     bool blocked_relink = false;
     bool pack = false;
+    bool small = false;
 };
 static thread_local ProfState g_prof;
 
@@ -256,7 +257,7 @@ static int ceil_log2(int64_t x) {
 // Enqueue the whole sort on stream s.  Returns PBIT_ECUDA if a launch failed.
 pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const ListDesc *tmpl,
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s,
-                         int sms, int64_t *launches) {
+                         int sms, int64_t *launches, bool small_lists) {
     int64_t n = 0;  // kernel launches
     prof_begin(s);
     if (ms.count < 0)
@@ -270,6 +271,18 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     Ctx cc = c;
     cc.M = M;
     launch_setup(cc, d_offsets, d_roots, mode, tmpl, s, sms);
+    if (small_lists && mode != 0) {
+        launch_small(cc, s, sms);
+        if (g_prof.on) {
+            g_prof.kb = cc.key_bytes;
+            g_prof.small = true;
+        }
+        if (launches)
+            *launches = 4;
+        return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
+    }
+    if (g_prof.on)
+        g_prof.small = false;
     launch_pack(cc, s, sms);
     if (cc.pack)
         ++n;
@@ -394,7 +407,7 @@ pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t
         d.root = single_root;
         d.id_base = 0;
         d.out_base = 0;
-        rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, &g_last_launches);
+        rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, &g_last_launches, single_n <= kSmallList);
     }
     *out = c;
     return rc;
@@ -554,7 +567,9 @@ int32_t pbit_profile_read(pbit_kernel_stat *out, int32_t max) {
             const char *nm = out[i].name;
             double b = 0;
             const double rec = kb == 8 ? 16.0 : 8.0;  // packed record
-            if (!std::strcmp(nm, "pack")) {
+            if (!std::strcmp(nm, "small")) {  // next + key read, order written
+                b = n * (8.0 + kb);
+            } else if (!std::strcmp(nm, "pack")) {
                 b = n * (4.0 + kb + rec);
             } else if (!std::strcmp(nm, "walk")) {
                 b = n * ((g_prof.pack ? rec : 4.0 + kb) + 4.0 + kb);

@@ -53,9 +53,11 @@ int device_sms();
 bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out);
 Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms);
 size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms);
+// small_lists: every list has at most kSmallList nodes (known on the host):
+// one kernel sorts each list in shared memory instead of the whole pipeline.
 pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const ListDesc *tmpl,
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s, int sms,
-                         int64_t *launches);
+                         int64_t *launches, bool small_lists = false);
 pbit_status map_status(int st);
 bool check_pool(const pbit_pool *p, int M, int K);
 bool prof_set(bool on);  // per-thread event profiling on/off; returns the previous state

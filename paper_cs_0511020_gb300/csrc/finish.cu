@@ -817,6 +817,14 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
     prof_mark("relink", s);
 }
 
+void launch_relink_direct(const Ctx &c, cudaStream_t s, int sms) {
+    const int64_t blocks = min((int64_t)sms * 16, max((int64_t)1, (c.ncap + 255) / 256));
+    k_relink<<<(unsigned)blocks, 256, 0, s>>>(c);
+    prof_mark("relink", s);
+    k_empty_roots<<<max(1, min(sms, (c.num_lists + 255) / 256)), 256, 0, s>>>(c);
+    prof_mark("relink", s);
+}
+
 void launch_check_done(const Ctx &c, int iters, cudaStream_t s) {
     k_check_done<<<1, 32, 0, s>>>(c, iters);
     prof_mark("plan", s);

@@ -95,7 +95,7 @@ extern "C" pbit_status pbit_sort_list_noalloc(const pbit_pool *pool, int32_t roo
     d.out_base = 0;
     cudaStream_t s = (cudaStream_t)stream;
     const bool prof = prof_set(false);  // no timing events (creating them allocates)
-    rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, nullptr);
+    rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, nullptr, n <= kSmallList);
     prof_set(prof);
     if (rc != PBIT_OK)
         return rc;

@@ -59,7 +59,9 @@ constexpr int kMaxIters = 64;
 // Buckets of (cutoff, kMidCap] nodes are finished by one CTA each in shared
 // memory instead of going through further global passes.
 constexpr int kMidCap = 4096;
-constexpr int kMidSpan = 16;  // ... when at most this many of their key bits vary (4 windows)
+constexpr int kMidSpan = 16;
+// Lists of at most kSmallList nodes are sorted by one kernel, one CTA each.
+constexpr int kSmallList = 4096;  // ... when at most this many of their key bits vary (4 windows)
 
 // Work counters that many CTAs hit at once sit on their own 128-byte lines
 // (an atomic on a line is serialized in one L2 slice).
@@ -351,6 +353,8 @@ void launch_setup(const Ctx &c, const int64_t *d_offsets, const int32_t *d_roots
                   const ListDesc *host_desc_tmpl, cudaStream_t s, int sms);
 void launch_pack(const Ctx &c, cudaStream_t s, int sms);
 void launch_walk(const Ctx &c, cudaStream_t s, int sms);
+void launch_small(const Ctx &c, cudaStream_t s, int sms);  // every list <= kSmallList nodes
+void launch_relink_direct(const Ctx &c, cudaStream_t s, int sms);
 void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds);
 void launch_validate_emit(const Ctx &c, cudaStream_t s, int sms);
 void launch_plan_init(const Ctx &c, cudaStream_t s);

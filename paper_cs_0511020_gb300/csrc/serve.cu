@@ -138,7 +138,10 @@ static pbit_status launch_batch(SrvSlot &slot, const std::vector<SrvReq *> &b, i
     if (cudaMemcpyAsync(c.desc, slot.h_desc, sizeof(ListDesc) * (size_t)L, cudaMemcpyHostToDevice, slot.stream) !=
         cudaSuccess)
         return PBIT_ECUDA;
-    pbit_status rc = enqueue_sort(c, ms, 1, nullptr, nullptr, nullptr, r0->M, slot.stream, sms, nullptr);
+    bool small = true;  // every request short: one kernel sorts each in shared memory
+    for (int i = 0; i < L; ++i)
+        small &= b[i]->n <= kSmallList;
+    pbit_status rc = enqueue_sort(c, ms, 1, nullptr, nullptr, nullptr, r0->M, slot.stream, sms, nullptr, small);
     if (rc != PBIT_OK)
         return rc;
     if (cudaMemcpyAsync(slot.h_out, c.status, 4, cudaMemcpyDeviceToHost, slot.stream) != cudaSuccess ||

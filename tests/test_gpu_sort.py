@@ -355,3 +355,82 @@ def test_mid_size_buckets_batched(pb):
         want, wr, _ = O.pbit_sort(sub_next, key[a:b], roots[i] - a, 16, 4)
         assert nr[i] == wr + a
         assert (got[a:b] == np.where(want >= 0, want + a, -1)).all(), f"list {i}"
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 1000, 4095, 4096])
+@pytest.mark.parametrize("kb", [1, 2, 4, 8])
+def test_short_list_kernel(pb, n, kb):
+    """Lists of at most 4096 nodes are sorted by one kernel (one CTA per list):
+    same result as the oracle, for every key width."""
+    nxt, root = I.random_list(n, 220 + n + kb)
+    key = I.uniform_keys(n, kb, 221 + n + kb)
+    if n > 4:
+        key[::7] = key[3]
+    _check_vs_oracle(pb, nxt, key, root, 8 * kb)
+
+
+@pytest.mark.parametrize("variant", ["signed", "descending", "float", "aos", "doubly", "M_below", "push"])
+def test_short_list_kernel_variants(pb, variant):
+    n = 3001
+    nxt, root = I.random_list(n, 230)
+    key = I.uniform_keys(n, 4, 231)
+    key[::5] = key[2]
+    if variant in ("signed", "descending"):
+        f = pb.SIGNED if variant == "signed" else pb.DESCENDING
+        st, got, r = _gpu_sort(pb, nxt, key, root, 32, 4, flags=f)
+        want, wr = O.stable_sort_definition(nxt, key, root, 32, signed=variant == "signed",
+                                            descending=variant == "descending")
+        assert st == pb.OK and r == wr and (got == want).all()
+    elif variant == "float":
+        vals = I.rng(232).standard_normal(n).astype(np.float32)
+        vals[::9] = -0.0
+        st, got, r = _gpu_sort(pb, nxt, vals.view(np.uint32), root, 32, 4, flags=pb.FLOAT)
+        order_in = O.list_order(nxt, root)
+        v = vals[order_in]
+        perm = np.lexsort((np.arange(n), np.signbit(v) == False, v))  # noqa: E712
+        want, wr = O.relink(nxt, order_in[perm])
+        assert st == pb.OK and r == wr and (got == want).all()
+    elif variant == "aos":
+        nodes = torch.from_numpy(I.aos_pack(nxt, key)).cuda()
+        st, r = pb.sort_pool_list(pb.make_pool_aos(nodes), root, n, 32, 4, check=False)
+        want, wr, _ = O.pbit_sort(nxt, key, root, 32, 4)
+        assert st == pb.OK and r == wr and (nodes[:, 0].cpu().numpy() == want).all()
+    elif variant == "doubly":
+        prev = np.full(n, -1, np.int32)
+        order = O.list_order(nxt, root)
+        prev[order[1:]] = order[:-1]
+        d_next, d_prev = torch.from_numpy(nxt.copy()).cuda(), torch.from_numpy(prev.copy()).cuda()
+        r = pb.sort_list(d_next, _dev_key(key), root, M=32, K=4, prev_t=d_prev)
+        got, gp = d_next.cpu().numpy(), d_prev.cpu().numpy()
+        want, wr, _ = O.pbit_sort(nxt, key, root, 32, 4)
+        assert r == wr and (got == want).all()
+        out = O.list_order(got, r)
+        assert gp[out[0]] == -1 and (gp[out[1:]] == out[:-1]).all()
+    elif variant == "M_below":
+        _check_vs_oracle(pb, nxt, I.uniform_keys(n, 8, 233), root, 24)
+    else:
+        nxt, root = I.push_built_list(n)
+        _check_vs_oracle(pb, nxt, key, root, 32)
+
+
+@pytest.mark.parametrize("case", ["cycle", "range", "short", "root", "self"])
+def test_short_list_kernel_malformed_untouched(pb, case):
+    n = 2500
+    nxt, root = I.random_list(n, 240)
+    key = I.uniform_keys(n, 4, 241)
+    bad = nxt.copy()
+    order = O.list_order(nxt, root)
+    if case == "cycle":
+        bad[order[-1]] = order[7]
+    elif case == "range":
+        bad[order[100]] = n + 5
+    elif case == "short":
+        bad[order[n - 10]] = -1
+    elif case == "self":
+        bad[order[50]] = order[50]
+    else:
+        root = n + 3
+    d_next = torch.from_numpy(bad.copy()).cuda()
+    st, _ = pb.sort_pool_list(pb.make_pool(d_next, _dev_key(key)), root, n, 32, 4, check=False)
+    assert st == pb.EBADLIST
+    assert (d_next.cpu().numpy() == bad).all()
