@@ -266,6 +266,7 @@ __device__ __forceinline__ bool stage_bucket(const Ctx &c, const Fin &f, KeyT *p
 // the other staging buffer.
 template <typename KeyT>
 __global__ void __launch_bounds__(32 * kFWarps) k_finish(Ctx c) {
+    griddep_wait();
     __shared__ __align__(16) KeyT s_key[kFWarps][2][kFinCap];
     __shared__ int32_t s_idx[kFWarps][2][kFinCap];
     if (*(volatile int32_t *)c.status)
@@ -356,6 +357,7 @@ struct MidLayout {
 
 template <typename KeyT>
 __global__ void __launch_bounds__(kMidTPB, 2) k_finish_mid(Ctx c) {
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char msm[];
     using U = typename KeyWord<KeyT>::U;
     using L = MidLayout<KeyT>;
@@ -547,6 +549,7 @@ __global__ void __launch_bounds__(kMidTPB, 2) k_finish_mid(Ctx c) {
 // next[s[q]] = s[q+1] straight into the pool (scattered 4-byte stores).  Used
 // when the lists live in different pools (the request server).
 __global__ void k_relink(Ctx c) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     const int32_t nv = c.ctr->n_virt;
@@ -641,6 +644,7 @@ __device__ int rel_excl_scan(int v, int *total, int *sh /* >= 33 ints */) {
 }
 
 __global__ void __launch_bounds__(kRelTPB) k_relink_part(Ctx c, int rb) {
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char rel_smem[];
     RelSmem &S = *reinterpret_cast<RelSmem *>(rel_smem);
     __shared__ int sh[40];
@@ -748,6 +752,7 @@ __global__ void __launch_bounds__(kRelTPB) k_relink_part(Ctx c, int rb) {
 // Apply the pairs of node block b0: one launch per window so the stores in
 // flight stay inside a few MB of next[].
 __global__ void k_relink_apply(Ctx c, int rb, int b0) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     const int32_t *tv = c.idxb[0], *ts = c.idxb[1];
@@ -760,6 +765,7 @@ __global__ void k_relink_apply(Ctx c, int rb, int b0) {
 }
 
 __global__ void k_empty_roots(Ctx c) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.num_lists; i += gridDim.x * blockDim.x)
@@ -770,6 +776,7 @@ __global__ void k_empty_roots(Ctx c) {
 // Every node must have been placed by a pass or by the finish: any segment
 // still live after the last pass means the pass budget was too small.
 __global__ void k_check_done(Ctx c, int iters) {
+    griddep_wait();
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         const int p = iters & 1;
         if (c.ctr->act_count[p] != 0 || c.ctr->pend_count[p] != 0)
@@ -783,11 +790,11 @@ static void launch_finish_t(const Ctx &c, cudaStream_t s, int sms) {
         const int smem = MidLayout<KeyT>::kTotal;
         cudaFuncSetAttribute(k_finish_mid<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         const int per_sm = max(1, min(4, (220 * 1024) / (smem + 2048)));
-        k_finish_mid<KeyT><<<(unsigned)(sms * per_sm), kMidTPB, smem, s>>>(c);
+        launch_pdl(k_finish_mid<KeyT>, dim3((unsigned)(sms * per_sm)), dim3(kMidTPB), smem, s, c);
     }
     const int smem = (int)(kFWarps * 2 * kFinCap * (sizeof(KeyT) + 4));
     const int per_sm = max(1, min(16, (200 * 1024) / smem));
-    k_finish<KeyT><<<(unsigned)(sms * per_sm), 32 * kFWarps, 0, s>>>(c);
+    launch_pdl(k_finish<KeyT>, dim3((unsigned)(sms * per_sm)), dim3(32 * kFWarps), 0, s, c);
     prof_mark("finish", s);
 }
 
@@ -803,30 +810,30 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
         const int64_t pblocks = min((int64_t)sms * 4, max((int64_t)1, (c.ncap + kRelTile - 1) / kRelTile));
         const int smem = (int)sizeof(RelSmem);
         cudaFuncSetAttribute(k_relink_part, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_relink_part<<<(unsigned)pblocks, kRelTPB, smem, s>>>(c, rb);
+        launch_pdl(k_relink_part, dim3((unsigned)pblocks), dim3(kRelTPB), smem, s, c, rb);
         const int64_t ablocks = min((int64_t)sms * 8, (int64_t)(((1ll << rb) + 255) / 256));
         const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
         for (int b = 0; b < nb; ++b)
-            k_relink_apply<<<(unsigned)ablocks, 256, 0, s>>>(c, rb, b);
+            launch_pdl(k_relink_apply, dim3((unsigned)ablocks), dim3(256), 0, s, c, rb, b);
     } else {
         const int64_t blocks = min((int64_t)sms * 16, max((int64_t)1, (c.ncap + 255) / 256));
-        k_relink<<<(unsigned)blocks, 256, 0, s>>>(c);
+        launch_pdl(k_relink, dim3((unsigned)blocks), dim3(256), 0, s, c);
     }
     prof_mark("relink", s);
-    k_empty_roots<<<max(1, min(sms, (c.num_lists + 255) / 256)), 256, 0, s>>>(c);
+    launch_pdl(k_empty_roots, dim3(max(1, min(sms, (c.num_lists + 255) / 256))), dim3(256), 0, s, c);
     prof_mark("relink", s);
 }
 
 void launch_relink_direct(const Ctx &c, cudaStream_t s, int sms) {
     const int64_t blocks = min((int64_t)sms * 16, max((int64_t)1, (c.ncap + 255) / 256));
-    k_relink<<<(unsigned)blocks, 256, 0, s>>>(c);
+    launch_pdl(k_relink, dim3((unsigned)blocks), dim3(256), 0, s, c);
     prof_mark("relink", s);
-    k_empty_roots<<<max(1, min(sms, (c.num_lists + 255) / 256)), 256, 0, s>>>(c);
+    launch_pdl(k_empty_roots, dim3(max(1, min(sms, (c.num_lists + 255) / 256))), dim3(256), 0, s, c);
     prof_mark("relink", s);
 }
 
 void launch_check_done(const Ctx &c, int iters, cudaStream_t s) {
-    k_check_done<<<1, 32, 0, s>>>(c, iters);
+    launch_pdl(k_check_done, dim3(1), dim3(32), 0, s, c, iters);
     prof_mark("plan", s);
 }
 

@@ -138,6 +138,7 @@ __device__ __forceinline__ unsigned long long low_mask(int bits) {
 // Lists become the first segments: empty lists vanish, lists up to the
 // cutoff go straight to the shared-memory finish, the rest are pending.
 __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
+    griddep_wait();
     __shared__ int sh[40];
     __shared__ int s_fin_base, s_pend_base, s_tile_base, s_mid_base;
     if (*(volatile int32_t *)c.status)
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
 // the rows the previous pass filled), and the AND/OR of the segment's keys.
 template <typename KeyT>
 __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
+    griddep_wait();
     __shared__ uint32_t s_cnt[kBins];
     __shared__ unsigned long long s_and, s_or;
     __shared__ int s_tile, s_aseg;
@@ -320,6 +322,7 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
 
 // ---------------------------------------------------------- plan_pending
 __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
+    griddep_wait();
     __shared__ int sh[40];
     __shared__ int s_act_base, s_re_base, s_re_tiles, s_tile_base, s_chunk_base, s_nrow_base;
     if (*(volatile int32_t *)c.status)
@@ -476,6 +479,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
 // segment, replace each tile's counts by the exclusive prefix within the
 // chunk and record the chunk totals.
 __global__ void __launch_bounds__(kTPB) k_tile_scan(Ctx c, int it) {
+    griddep_wait();
     __shared__ uint32_t sh[(kTPB / 32 + 1) * kBins];
     if (*(volatile int32_t *)c.status)
         return;
@@ -526,6 +530,7 @@ __global__ void __launch_bounds__(kTPB) k_tile_scan(Ctx c, int it) {
 // its chunks (in place) and the segment's digit histogram.  A segment of one
 // tile has no chunk: its histogram is its tile's row.
 __global__ void __launch_bounds__(kTPB) k_chunk_scan(Ctx c, int it) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1;
@@ -612,6 +617,7 @@ __device__ __forceinline__ void pass_issue(const Ctx &c, int cur, int g, int st,
 // positions from the scanned counts.
 template <typename KeyT>
 __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx c, int it) {
+    griddep_wait();
     extern __shared__ __align__(128) unsigned char smem[];
     PassSmem &S = *reinterpret_cast<PassSmem *>(smem);
     unsigned char *stages = smem + PassLayout<KeyT>::kHdr;
@@ -902,6 +908,7 @@ __device__ __forceinline__ int classify_bucket(const Ctx &c, int cur, int s, con
 // per active segment: how many next-active, pending, small/done buckets and
 // stats tiles its buckets produce
 __global__ void k_plan_count(Ctx c, int it) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1;
@@ -927,6 +934,7 @@ __global__ void k_plan_count(Ctx c, int it) {
 
 // exclusive scan of the per-segment counts (one CTA), new counters
 __global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
+    griddep_wait();
     __shared__ int sh[40];
     __shared__ int s_a, s_p, s_f, s_t, s_m;
     if (*(volatile int32_t *)c.status)
@@ -996,6 +1004,7 @@ __global__ void __launch_bounds__(1024) k_plan_scan(Ctx c, int it) {
 }
 
 __global__ void k_plan_write(Ctx c, int it) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1, nxt = cur ^ 1;
@@ -1046,23 +1055,23 @@ static void launch_iter_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     cudaFuncSetAttribute(k_pass<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int per_sm = PassLayout<KeyT>::kMinBlocks;
     const unsigned pblocks = (unsigned)max(1, min(sms * 4, (int)((c.seg_cap + 255) / 256)));
-    k_seg_stats<KeyT><<<sms * 4, kTPB, 0, s>>>(c, it);
+    launch_pdl(k_seg_stats<KeyT>, dim3(sms * 4), dim3(kTPB), 0, s, c, it);
     prof_mark("seg_stats", s);
-    k_plan_pending<<<1, 1024, 0, s>>>(c, it);
+    launch_pdl(k_plan_pending, dim3(1), dim3(1024), 0, s, c, it);
     prof_mark("plan", s);
-    k_tile_scan<<<sms * 4, kTPB, 0, s>>>(c, it);
-    k_chunk_scan<<<sms * 4, kTPB, 0, s>>>(c, it);
+    launch_pdl(k_tile_scan, dim3(sms * 4), dim3(kTPB), 0, s, c, it);
+    launch_pdl(k_chunk_scan, dim3(sms * 4), dim3(kTPB), 0, s, c, it);
     prof_mark("scan", s);
-    k_pass<KeyT><<<sms * per_sm, kTPB, smem, s>>>(c, it);
+    launch_pdl(k_pass<KeyT>, dim3(sms * per_sm), dim3(kTPB), smem, s, c, it);
     prof_mark("pass", s);
-    k_plan_count<<<pblocks, 256, 0, s>>>(c, it);
-    k_plan_scan<<<1, 1024, 0, s>>>(c, it);
-    k_plan_write<<<pblocks, 256, 0, s>>>(c, it);
+    launch_pdl(k_plan_count, dim3(pblocks), dim3(256), 0, s, c, it);
+    launch_pdl(k_plan_scan, dim3(1), dim3(1024), 0, s, c, it);
+    launch_pdl(k_plan_write, dim3(pblocks), dim3(256), 0, s, c, it);
     prof_mark("plan", s);
 }
 
 void launch_plan_init(const Ctx &c, cudaStream_t s) {
-    k_plan_init<<<1, 1024, 0, s>>>(c);
+    launch_pdl(k_plan_init, dim3(1), dim3(1024), 0, s, c);
     prof_mark("plan", s);
 }
 

@@ -22,6 +22,7 @@ namespace pbit {
 // mode 2: a single list described by t
 __global__ void __launch_bounds__(1024) k_setup(Ctx c, ListDesc t, const int64_t *offsets,
                                                 const int32_t *roots, int mode) {
+    griddep_wait();
     __shared__ int32_t s_nvirt;
     __shared__ int32_t s_bad;
     const int L = c.num_lists;
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(1024) k_setup(Ctx c, ListDesc t, const int64_t
 // constant shift; per-list pools (serving) look the list up.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_pack(Ctx c) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     const int64_t nv = c.ctr->n_virt;
@@ -185,6 +187,7 @@ __device__ __forceinline__ void flush_group(const Ctx &c, KeyT *ckey, int64_t ba
 
 template <typename KeyT>
 __global__ void __launch_bounds__(256, 6) k_walk(Ctx c) {
+    griddep_wait();
     __shared__ int32_t s_i[256 * kStagePad];
     __shared__ KeyT s_k[256 * kStagePad];
     if (*(volatile int32_t *)c.status)
@@ -378,6 +381,7 @@ __device__ __forceinline__ int64_t wy_pack(int32_t succ, uint32_t v) {
 }
 
 __global__ void k_ruler_walk(Ctx c) {
+    griddep_wait();
     const int32_t nreg = (c.Rcap + 31) / 32;  // walks started at tasks 0, 32, 64, ...
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < c.Scap;
          w += (int64_t)gridDim.x * blockDim.x) {
@@ -419,6 +423,7 @@ __global__ void k_ruler_walk(Ctx c) {
 
 // One pointer-jumping round over the walks: (s, v) <- (succ(s), v + v(s)).
 __global__ void k_wy_round(const int64_t *a, int64_t *b, int32_t n) {
+    griddep_wait();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         uint64_t x = (uint64_t)a[t];
         const int32_t s = (int32_t)(x >> 32);
@@ -434,6 +439,7 @@ __global__ void k_wy_round(const int64_t *a, int64_t *b, int32_t n) {
 // Every task: (end of its chain, suffix length) from its walk's.  A task no
 // walk reached (only in a malformed list) gets succ -2.
 __global__ void k_ruler_expand(Ctx c, int fin) {
+    griddep_wait();
     const int64_t *sw = c.sw[fin];
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < c.Rcap;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -452,6 +458,7 @@ __global__ void k_ruler_expand(Ctx c, int fin) {
 
 // --------------------------------------------------------- validate + emit
 __global__ void k_validate(Ctx c) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     const int64_t *w = c.wy[0];
@@ -476,6 +483,7 @@ __global__ void k_validate(Ctx c) {
 // time with all loads issued before the stores.
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_emit(Ctx c) {
+    griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
     const int lane = threadIdx.x & 31;
@@ -544,7 +552,7 @@ void launch_setup(const Ctx &c, const int64_t *d_offsets, const int32_t *d_roots
     ListDesc t{};
     if (tmpl)
         t = *tmpl;
-    k_setup<<<1, 1024, 0, s>>>(c, t, d_offsets, d_roots, mode);
+    launch_pdl(k_setup, dim3(1), dim3(1024), 0, s, c, t, d_offsets, d_roots, mode);
     prof_mark("setup", s);
 }
 
@@ -553,10 +561,10 @@ void launch_pack(const Ctx &c, cudaStream_t s, int sms) {
         return;
     const unsigned blocks = (unsigned)max((int64_t)1, min((int64_t)sms * 8, (c.ncap + 255) / 256));
     switch (c.key_bytes) {
-    case 1: k_pack<uint8_t><<<blocks, 256, 0, s>>>(c); break;
-    case 2: k_pack<uint16_t><<<blocks, 256, 0, s>>>(c); break;
-    case 4: k_pack<uint32_t><<<blocks, 256, 0, s>>>(c); break;
-    default: k_pack<unsigned long long><<<blocks, 256, 0, s>>>(c); break;
+    case 1: launch_pdl(k_pack<uint8_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    case 2: launch_pdl(k_pack<uint16_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    case 4: launch_pdl(k_pack<uint32_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    default: launch_pdl(k_pack<unsigned long long>, dim3(blocks), dim3(256), 0, s, c); break;
     }
     prof_mark("pack", s);
 }
@@ -565,37 +573,37 @@ void launch_walk(const Ctx &c, cudaStream_t s, int sms) {
     const int64_t warps_needed = (c.Rcap + 31) / 32;  // at least one task per lane
     const unsigned blocks = (unsigned)min((int64_t)sms * 8, max((int64_t)1, (warps_needed + 7) / 8));
     switch (c.key_bytes) {
-    case 1: k_walk<uint8_t><<<blocks, 256, 0, s>>>(c); break;
-    case 2: k_walk<uint16_t><<<blocks, 256, 0, s>>>(c); break;
-    case 4: k_walk<uint32_t><<<blocks, 256, 0, s>>>(c); break;
-    default: k_walk<unsigned long long><<<blocks, 256, 0, s>>>(c); break;
+    case 1: launch_pdl(k_walk<uint8_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    case 2: launch_pdl(k_walk<uint16_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    case 4: launch_pdl(k_walk<uint32_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    default: launch_pdl(k_walk<unsigned long long>, dim3(blocks), dim3(256), 0, s, c); break;
     }
     prof_mark("walk", s);
 }
 
 void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds) {
     const int64_t wb = min((int64_t)sms * 8, max((int64_t)1, ((int64_t)c.Scap + 127) / 128));
-    k_ruler_walk<<<(unsigned)wb, 128, 0, s>>>(c);
+    launch_pdl(k_ruler_walk, dim3((unsigned)wb), dim3(128), 0, s, c);
     prof_mark("wyllie", s);
     const int64_t rb = min((int64_t)sms * 8, max((int64_t)1, ((int64_t)c.Scap + 255) / 256));
     for (int r = 0; r < rounds; ++r) {
-        k_wy_round<<<(unsigned)rb, 256, 0, s>>>(c.sw[r & 1], c.sw[(r & 1) ^ 1], c.Scap);
+        launch_pdl(k_wy_round, dim3((unsigned)rb), dim3(256), 0, s, c.sw[r & 1], c.sw[(r & 1) ^ 1], c.Scap);
         prof_mark("wyllie", s);
     }
     const int64_t eb = min((int64_t)sms * 8, max((int64_t)1, ((int64_t)c.Rcap + 255) / 256));
-    k_ruler_expand<<<(unsigned)eb, 256, 0, s>>>(c, rounds & 1);
+    launch_pdl(k_ruler_expand, dim3((unsigned)eb), dim3(256), 0, s, c, rounds & 1);
     prof_mark("wyllie", s);
 }
 
 void launch_validate_emit(const Ctx &c, cudaStream_t s, int sms) {
-    k_validate<<<max(1, min(sms, (c.num_lists + 255) / 256)), 256, 0, s>>>(c);
+    launch_pdl(k_validate, dim3(max(1, min(sms, (c.num_lists + 255) / 256))), dim3(256), 0, s, c);
     prof_mark("validate", s);
     unsigned blocks = (unsigned)(sms * 8);
     switch (c.key_bytes) {
-    case 1: k_emit<uint8_t><<<blocks, 256, 0, s>>>(c); break;
-    case 2: k_emit<uint16_t><<<blocks, 256, 0, s>>>(c); break;
-    case 4: k_emit<uint32_t><<<blocks, 256, 0, s>>>(c); break;
-    default: k_emit<unsigned long long><<<blocks, 256, 0, s>>>(c); break;
+    case 1: launch_pdl(k_emit<uint8_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    case 2: launch_pdl(k_emit<uint16_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    case 4: launch_pdl(k_emit<uint32_t>, dim3(blocks), dim3(256), 0, s, c); break;
+    default: launch_pdl(k_emit<unsigned long long>, dim3(blocks), dim3(256), 0, s, c); break;
     }
     prof_mark("emit", s);
 }

@@ -36,6 +36,7 @@ struct SmallLayout {
 
 template <typename KeyT>
 __global__ void __launch_bounds__(kSmallTPB) k_small_sort(Ctx c) {
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char ssm[];
     using U = typename KeyWord<KeyT>::U;
     using L = SmallLayout<KeyT>;
@@ -250,7 +251,7 @@ static void launch_small_t(const Ctx &c, cudaStream_t s, int sms) {
     const int smem = SmallLayout<KeyT>::kTotal;
     cudaFuncSetAttribute(k_small_sort<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int blocks = max(1, min(c.num_lists, sms * 2));
-    k_small_sort<KeyT><<<(unsigned)blocks, kSmallTPB, smem, s>>>(c);
+    launch_pdl(k_small_sort<KeyT>, dim3((unsigned)blocks), dim3(kSmallTPB), smem, s, c);
 }
 
 void launch_small(const Ctx &c, cudaStream_t s, int sms) {
