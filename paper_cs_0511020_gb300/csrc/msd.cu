@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
     griddep_wait();
     __shared__ uint32_t s_cnt[kBins];
     __shared__ unsigned long long s_and, s_or;
-    __shared__ int s_tile, s_aseg;
+    __shared__ int s_aseg;
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1;
@@ -240,14 +240,9 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         s_or = 0ull;
         s_aseg = -1;
     }
-    while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0)
-            s_tile = atomicAdd(&c.ctr->stat_ctr[it], 1);
-        __syncthreads();
-        const int g = s_tile;
-        if (g >= ntiles)
-            break;
+    // tiles in a static grid-stride order (uniform work: no claiming counter)
+    for (int g = blockIdx.x; g < ntiles; g += gridDim.x) {
+        __syncthreads();  // the previous tile's counts are stored and cleared
         const int s = upper_index(c.pend_tile_base[cur], P, g);
         if (threadIdx.x == 0 && s != s_aseg) {  // AND/OR are merged per segment, not per tile
             if (s_aseg >= 0) {
@@ -258,6 +253,7 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
             s_or = 0ull;
             s_aseg = s;
         }
+        __syncthreads();  // the reset above precedes this tile's merges into s_and / s_or
         const Seg sg = c.pend[cur][s];
         const int k = g - c.pend_tile_base[cur][s];
         const int64_t b0 = (int64_t)sg.start + (int64_t)k * kTile;
@@ -266,21 +262,22 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         const int hi = sg.hi, lo = max(hi - kD, 0);
         const unsigned dmask = (1u << (hi - lo)) - 1u;
         my_elems += cnt;
-        unsigned long long kv[kItems];
+        using U = typename KeyWord<KeyT>::U;  // 32-bit words for keys up to 4 bytes
+        U kv[kItems];
 #pragma unroll
         for (int u = 0; u < kItems; ++u) {
             const int pos = wid * 32 * kItems + u * 32 + lane;
-            kv[u] = pos < cnt ? (unsigned long long)keys[b0 + pos] : 0ull;
+            kv[u] = pos < cnt ? (U)keys[b0 + pos] : (U)0;
         }
         uint32_t wc = 0;
-        unsigned long long a_and = ~0ull, a_or = 0ull;
+        U w_and = ~(U)0, w_or = 0;
 #pragma unroll
         for (int u = 0; u < kItems; ++u) {
             const int pos = wid * 32 * kItems + u * 32 + lane;
             const bool valid = pos < cnt;
             if (valid) {
-                a_and &= kv[u];
-                a_or |= kv[u];
+                w_and &= kv[u];
+                w_or |= kv[u];
             }
             const unsigned dig = (unsigned)(kv[u] >> lo) & dmask;
             unsigned m = __ballot_sync(kFull, valid);
@@ -293,9 +290,10 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            a_and &= __shfl_xor_sync(kFull, a_and, o);
-            a_or |= __shfl_xor_sync(kFull, a_or, o);
+            w_and &= __shfl_xor_sync(kFull, w_and, o);
+            w_or |= __shfl_xor_sync(kFull, w_or, o);
         }
+        const unsigned long long a_and = (unsigned long long)w_and, a_or = (unsigned long long)w_or;
         if (lane < kBins && wc)
             atomicAdd(&s_cnt[lane], wc);
         if (lane == 0) {
@@ -1055,7 +1053,7 @@ static void launch_iter_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     cudaFuncSetAttribute(k_pass<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     const int per_sm = PassLayout<KeyT>::kMinBlocks;
     const unsigned pblocks = (unsigned)max(1, min(sms * 4, (int)((c.seg_cap + 255) / 256)));
-    launch_pdl(k_seg_stats<KeyT>, dim3(sms * 4), dim3(kTPB), 0, s, c, it);
+    launch_pdl(k_seg_stats<KeyT>, dim3(sms * 8), dim3(kTPB), 0, s, c, it);
     prof_mark("seg_stats", s);
     launch_pdl(k_plan_pending, dim3(1), dim3(1024), 0, s, c, it);
     prof_mark("plan", s);
