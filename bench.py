@@ -310,13 +310,15 @@ def run_ours(a):
         m, dt = oracle_sample(a.cpu_sample_log2n, 0x0511020 + 2, a.key_bits)
         cpu = {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the oracle (single-threaded literal Pbit) on one 2^{a.cpu_sample_log2n}-node list "
-                         f"of the same recipe ({dt:.1f} s)"}
+                         f"of the same recipe ({dt:.1f} s)",
+               "k_sweep_ms": oracle_k_sweep()}
     del d_next0, d_next, d_key, ws_h, h_next0, h_next, h_key
     torch.cuda.empty_cache()
     batched = None if (a.no_batched or world > 1) else run_batched(a, torch, pbit, I, local)
     torch.cuda.empty_cache()
     serve = None if (a.no_serve or world > 1) else run_serve(a, torch, pbit, I, local)
     torch.cuda.empty_cache()
+    k_sweep = None if world > 1 else run_k_sweep(a, torch, pbit, I)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -334,6 +336,7 @@ def run_ours(a):
         "cpu_baseline": cpu,
         "batched": batched,
         "serve": serve,
+        "k_sweep": k_sweep,
         "clocks": clocks,
         "wall_s": wall,
     }
@@ -488,6 +491,54 @@ def run_serve(a, torch, pbit, I, local=0):
             "fifo_per_list": fifo,
             "latency": "completion seen by the scheduler (served) or after the synchronous call returns "
                        "(FIFO) minus the scheduled arrival, host monotonic clock"}
+
+
+K_SWEEP = (1, 2, 4, 8, 16)
+
+
+def run_k_sweep(a, torch, pbit, I):
+    """The paper's digit width K (its Sec. on the length of the bit pattern)
+    swept on the GPU: one 2^24-node uint32 list, M=32, median of 5 sorts per
+    K.  The result is K-independent and so is the GPU's work (its own digit
+    width is fixed); the literal oracle's time per K is in cpu_baseline."""
+    n = 1 << 24
+    gen = torch.Generator(device="cuda").manual_seed(I.SEED_BASE + 24)
+    d_next0, root = I.device_random_list(n, gen)
+    d_key = I.device_keys(n, 4, gen)
+    d_next = d_next0.clone()
+    pool = pbit.make_pool(d_next, d_key)
+    ws = pbit.alloc_workspace(pbit.workspace_size(n, 1, 4))
+    stream = torch.cuda.current_stream()
+    out = {}
+    for K in K_SWEEP:
+        t = []
+        for rep in range(6):
+            d_next.copy_(d_next0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pbit.sort_pool_list(pool, root, n, 32, K, ws=ws, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep:
+                t.append(e0.elapsed_time(e1))
+        out[str(K)] = statistics.median(t)
+    return {"workload": "one 2^24-node SoA uint32 list, random order, uniform keys, M=32", "gpu_ms": out}
+
+
+def oracle_k_sweep():
+    """The literal oracle's time per K on one 2^18-node list (it visits every
+    node M/K times: the paper's K experiment)."""
+    from oracle import oracle as O
+    from paper_cs_0511020_gb300 import inputs as I
+    n = 1 << 18
+    nxt, root = I.random_list(n, 0x0511020 + 24)
+    key = I.uniform_keys(n, 4, 0x0511020 + 25)
+    res = {}
+    for K in K_SWEEP:
+        t0 = time.perf_counter()
+        O.pbit_sort(nxt, key, root, 32, K)
+        res[str(K)] = 1e3 * (time.perf_counter() - t0)
+    return {"n": n, "M": 32, "ms": res}
 
 
 def traffic_for(name, launches_per_step, log2n):

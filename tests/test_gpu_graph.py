@@ -113,3 +113,21 @@ def test_autotune_leaves_pool_and_tunes(pb):
     st, nr = pb.sort_pool_batched(pool, d_roots, d_off, 32, 4)
     assert st == pb.OK
     _check_batch(nxt, key, roots, off, d_next.cpu().numpy(), nr.cpu().numpy())
+
+
+def test_single_graph_short_list(pb):
+    """A short list's graph holds the one-kernel path; replays equal the oracle."""
+    n = 3000
+    nxt, root = I.random_list(n, 950)
+    key = I.uniform_keys(n, 2, 951)
+    d_next = torch.from_numpy(nxt.copy()).cuda()
+    d_key = torch.from_numpy(key.view(np.int16)).cuda()
+    g = pb.Graph.single_list(pb.make_pool(d_next, d_key), root, n, 16, 4)
+    want, wr, _ = O.pbit_sort(nxt, key, root, 16, 4)
+    for _ in range(3):
+        d_next.copy_(torch.from_numpy(nxt))
+        g.launch()
+        st, r = g.result()
+        assert st == pb.OK and r == wr and (d_next.cpu().numpy() == want).all()
+    assert g.node_count() < 20
+    g.close()
