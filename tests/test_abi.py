@@ -136,3 +136,27 @@ def test_tune_file_is_read_for_its_size_class(so, tmp_path):
     assert tuned_20 > default_20
     assert none_20 == tuned_20          # room for the stored choice
     assert none_24 == default_24        # another size class: built-in default
+
+
+def test_more_argument_checks_without_a_device(so):
+    """Host-side validation that returns before any CUDA call."""
+    from paper_cs_0511020_gb300 import pbit
+    L = pbit.lib()
+    nr = ctypes.c_int32(7)
+    empty = pbit.Pool(0x1000, 4, 0x2000, 4, 4, 0, 0, 0, 0)
+    assert L.pbit_sort_list(ctypes.addressof(empty), 3, 0, 32, 4, ctypes.byref(nr), None, None, 0, None) == pbit.EBADLIST
+    big = pbit.Pool(0x1000, 4, 0x2000, 4, 4, 0, pbit.NOALLOC_MAX_NODES + 1, 0, 0)
+    assert L.pbit_sort_list_noalloc(ctypes.addressof(big), 0, pbit.NOALLOC_MAX_NODES + 1, 32, 4, ctypes.byref(nr),
+                                    None) == pbit.ENOMEM
+    pool = pbit.Pool(0x1000, 4, 0x2000, 4, 4, 0, 100, 0, 0)
+    h = ctypes.c_void_p()
+    assert L.pbit_graph_create_single(ctypes.addressof(pool), 0, 100, 32, 5, None, None, 0, ctypes.byref(h)) == pbit.EINVAL
+    assert L.pbit_graph_create_single(ctypes.addressof(pool), 100, 100, 32, 4, None, None, 0, ctypes.byref(h)) == pbit.EBADLIST
+    assert L.pbit_graph_create_batched(ctypes.addressof(pool), 0, None, None, 32, 4, None, None, None, 0,
+                                       ctypes.byref(h)) == pbit.EINVAL
+    best = pbit.Tune()
+    assert L.pbit_autotune_batched(ctypes.addressof(pool), 1, 0x10, 0x20, 32, 4, 0x30, None, 0, 0, None,
+                                   ctypes.addressof(best), None) == pbit.EINVAL  # reps = 0
+    assert L.pbit_graph_launch(None, None) == pbit.EINVAL
+    assert L.pbit_graph_result(None, None, None) == pbit.EINVAL
+    assert L.pbit_graph_node_count(None) == 0
