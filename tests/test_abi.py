@@ -109,10 +109,10 @@ _TUNE_PROBE = """
 import json
 from paper_cs_0511020_gb300 import pbit
 n = 1 << 20
-print(json.dumps([pbit.workspace_size(n, 1, 4), pbit.workspace_size(n, 1, 4, {"smem_cutoff": 128, "ruler_stride": 16}),
-                  pbit.workspace_size(n, 1, 4, {"smem_cutoff": 512, "ruler_stride": 32}),
+print(json.dumps([pbit.workspace_size(n, 1, 4), pbit.workspace_size(n, 1, 4, {"smem_cutoff": 128, "ruler_stride": 4}),
+                  pbit.workspace_size(n, 1, 4, {"smem_cutoff": 512, "ruler_stride": 8}),
                   pbit.workspace_size(1 << 24, 1, 4),
-                  pbit.workspace_size(1 << 24, 1, 4, {"smem_cutoff": 512, "ruler_stride": 32})]))
+                  pbit.workspace_size(1 << 24, 1, 4, {"smem_cutoff": 512, "ruler_stride": 16})]))
 """
 
 
@@ -128,14 +128,14 @@ def test_tune_file_is_read_for_its_size_class(so, tmp_path):
     if torch.cuda.is_available():
         pytest.skip("device present: the entry below is keyed for the no-device fallback")
     f = tmp_path / "tune.txt"
-    f.write_text("garbage line\npbit-tune sms=148 cc=0 kb=4 lg_n=20 lg_l=0 cutoff=128 stride=16 ms=1.5\n")
+    f.write_text("garbage line\npbit-tune sms=148 cc=0 kb=4 lg_n=20 lg_l=0 cutoff=128 stride=4 ms=1.5\n")
     env = dict(os.environ, PBIT_TUNE_FILE=str(f))
     out = subprocess.run([sys.executable, "-c", _TUNE_PROBE], env=env, cwd=ROOT, capture_output=True, text=True,
                          check=True).stdout
     none_20, tuned_20, default_20, none_24, default_24 = json.loads(out.strip().splitlines()[-1])
-    assert tuned_20 > default_20
+    assert tuned_20 > default_20        # (the built-in default at 2^20 nodes: cutoff 512, stride 8)
     assert none_20 == tuned_20          # room for the stored choice
-    assert none_24 == default_24        # another size class: built-in default
+    assert none_24 == default_24        # another size class: built-in default (stride 16)
 
 
 def test_more_argument_checks_without_a_device(so):
