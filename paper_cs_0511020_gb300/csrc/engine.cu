@@ -1,9 +1,15 @@
 // engine.cu -- host orchestration and the C ABI of include/pbit.h.
 //
 // One sort call = one stream-ordered sequence:
-//   memsets -> setup -> walk -> wyllie rounds -> validate + emit
-//   -> plan_init -> ceil(M/D) x [seg_stats, plan_pending, pass, plan]
-//   -> check -> finish -> relink -> status read-back.
+//   memsets -> setup -> pack -> walk -> ruler walks + pointer jumping
+//   -> validate + emit -> plan_init
+//   -> ceil(M/D) x [seg_stats, plan_pending, tile_scan, chunk_scan, pass,
+//                   plan_count, plan_scan, plan_write]
+//   -> check -> CTA finish (mid buckets) -> warp finish (small buckets)
+//   -> relink -> status read-back;
+// or, when every list has at most kSmallList nodes (known on the host),
+//   memsets -> setup -> one-CTA-per-list sort -> direct relink.
+// Kernels are launched with programmatic stream serialization (launch_pdl).
 // The workspace is carved into fixed regions whose sizes depend only on the
 // pool size, the number of lists, the key width and the tune; no call
 // allocates device memory.

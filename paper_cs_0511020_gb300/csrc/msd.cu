@@ -20,7 +20,7 @@
 // One iteration (= one recursion level for every live segment):
 //   seg_stats     pending segments: per-tile counts of the window under their
 //                 top bit, and the AND/OR of their keys
-//   plan_pending  pending -> active / small / done / pending again (when the
+//   plan_pending  pending -> active / small / mid / done / pending again (when the
 //                 top window does not vary, the segment retries one window
 //                 lower, at its highest varying bit); tile, chunk and
 //                 next-row bases of all active segments
@@ -30,7 +30,8 @@
 //                 shared memory; fused: counts per next-pass tile and AND/OR
 //                 per output bucket
 //   plan_count / plan_scan / plan_write
-//                 output buckets -> next active / pending / small / done
+//                 output buckets -> next active / pending / small (warp
+//                 finish) / mid-size (CTA finish) / done
 #include "pbit_internal.cuh"
 
 namespace pbit {
