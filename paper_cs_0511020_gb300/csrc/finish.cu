@@ -595,7 +595,7 @@ __global__ void k_relink(Ctx c) {
 // groups its pairs by bucket in shared memory so that its writes to a
 // bucket are one contiguous run.
 constexpr int kRelTPB = 256;
-constexpr int kRelItems = 16;
+constexpr int kRelItems = 8;  // (16 took 108 registers: 2 CTAs per SM, latency-bound)
 constexpr int kRelTile = kRelTPB * kRelItems;
 constexpr int kMaxRelBuckets = 512;
 constexpr int kCursorStride = 32;  // one 128-byte line per bucket cursor
@@ -643,7 +643,7 @@ __device__ int rel_excl_scan(int v, int *total, int *sh /* >= 33 ints */) {
     return r;
 }
 
-__global__ void __launch_bounds__(kRelTPB) k_relink_part(Ctx c, int rb) {
+__global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char rel_smem[];
     RelSmem &S = *reinterpret_cast<RelSmem *>(rel_smem);
@@ -759,8 +759,28 @@ __global__ void k_relink_apply(Ctx c, int rb, int b0) {
     unsigned char *next = reinterpret_cast<unsigned char *>(c.desc[0].next);
     const int64_t stride = c.desc[0].next_stride;
     const int32_t cnt = c.rel_cursor[b0 * kCursorStride];
-    const int64_t base = (int64_t)b0 << rb;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+    const int64_t base = (int64_t)b0 << rb;  // a multiple of 2^20: 16-byte aligned runs
+    // 16 pairs per thread (four 16-byte loads per array), all loads issued
+    // before the stores: the kernel waits on its loads, so keep many in flight
+    const int64_t n16 = cnt >> 4;
+    const int4 *tv4 = reinterpret_cast<const int4 *>(tv + base), *ts4 = reinterpret_cast<const int4 *>(ts + base);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+        int4 v[4], s[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            v[u] = tv4[4 * i + u];
+            s[u] = ts4[4 * i + u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            *(int32_t *)(next + (int64_t)v[u].x * stride) = s[u].x;
+            *(int32_t *)(next + (int64_t)v[u].y * stride) = s[u].y;
+            *(int32_t *)(next + (int64_t)v[u].z * stride) = s[u].z;
+            *(int32_t *)(next + (int64_t)v[u].w * stride) = s[u].w;
+        }
+    }
+    for (int64_t i = 16 * n16 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
         *(int32_t *)(next + (int64_t)tv[base + i] * stride) = ts[base + i];
 }
 
@@ -811,7 +831,7 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
         const int smem = (int)sizeof(RelSmem);
         cudaFuncSetAttribute(k_relink_part, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         launch_pdl(k_relink_part, dim3((unsigned)pblocks), dim3(kRelTPB), smem, s, c, rb);
-        const int64_t ablocks = min((int64_t)sms * 8, (int64_t)(((1ll << rb) + 255) / 256));
+        const int64_t ablocks = min((int64_t)sms * 8, (int64_t)(((1ll << rb) / 16 + 255) / 256));
         const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
         for (int b = 0; b < nb; ++b)
             launch_pdl(k_relink_apply, dim3((unsigned)ablocks), dim3(256), 0, s, c, rb, b);

@@ -479,8 +479,10 @@ __global__ void k_validate(Ctx c) {
 
 // Each warp moves 32 chunks: lane l first fetches the metadata of chunk l
 // (task, offset in the task, the task's list and rank) so the dependent
-// metadata loads of 32 chunks overlap; then the chunks are copied four at a
-// time with all loads issued before the stores.
+// metadata loads of 32 chunks overlap; then the chunks are copied kEmitBatch
+// at a time with all loads issued before the stores (the kernel is bound by
+// load latency: more loads in flight per warp).
+constexpr int kEmitBatch = 8;
 template <typename KeyT>
 __global__ void __launch_bounds__(256) k_emit(Ctx c) {
     griddep_wait();
@@ -517,13 +519,13 @@ __global__ void __launch_bounds__(256) k_emit(Ctx c) {
             }
         }
         const int nc = (int)min((int64_t)32, nchunks - ch0);
-        for (int b = 0; b < nc; b += 4) {
-            int32_t vi[4];
-            KeyT vk[4];
-            int32_t pos[4];
-            bool ok[4];
+        for (int b = 0; b < nc; b += kEmitBatch) {
+            int32_t vi[kEmitBatch];
+            KeyT vk[kEmitBatch];
+            int32_t pos[kEmitBatch];
+            bool ok[kEmitBatch];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kEmitBatch; ++u) {
                 const int src = min(b + u, 31);
                 const int32_t cnt = __shfl_sync(kFull, m_cnt, src);
                 pos[u] = __shfl_sync(kFull, m_pos, src) + lane;
@@ -535,7 +537,7 @@ __global__ void __launch_bounds__(256) k_emit(Ctx c) {
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kEmitBatch; ++u) {
                 if (ok[u]) {
                     okey[pos[u]] = vk[u];
                     oidx[pos[u]] = vi[u];
