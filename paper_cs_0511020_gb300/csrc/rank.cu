@@ -573,7 +573,13 @@ void launch_pack(const Ctx &c, cudaStream_t s, int sms) {
 
 void launch_walk(const Ctx &c, cudaStream_t s, int sms) {
     const int64_t warps_needed = (c.Rcap + 31) / 32;  // at least one task per lane
-    const unsigned blocks = (unsigned)min((int64_t)sms * 8, max((int64_t)1, (warps_needed + 7) / 8));
+    // Once the records no longer fit in L2 the walk is bound by the rate of
+    // random DRAM accesses, which 32 warps per SM already reach; more only
+    // add contention (measured at 2^25 nodes, CTAs per SM: 2 -> 1.07 ms,
+    // 4 -> 0.87 ms, 6 -> 0.89 ms, 8 (1.33 waves) -> 0.99 ms).  Smaller pools,
+    // read from L2, keep the larger grid.
+    const int per_sm = c.ncap >= (1ll << 24) ? 4 : 8;
+    const unsigned blocks = (unsigned)min((int64_t)sms * per_sm, max((int64_t)1, (warps_needed + 7) / 8));
     switch (c.key_bytes) {
     case 1: launch_pdl(k_walk<uint8_t>, dim3(blocks), dim3(256), 0, s, c); break;
     case 2: launch_pdl(k_walk<uint16_t>, dim3(blocks), dim3(256), 0, s, c); break;
