@@ -164,6 +164,22 @@ pbit_status pbit_sort_list_noalloc(const pbit_pool *pool, int32_t root, int64_t 
 int64_t pbit_last_launch_count(void);
 
 /*
+ * Self-test of the bounded device wait (failure detection; not part of the
+ * method, which has no waits: the paper's sort is sequential).  One CTA
+ * waits on a shared-memory mbarrier that nothing ever completes, through the
+ * same bounded-wait routine with which the MSD pass waits for its tile
+ * copies, polling at most `iterations` times (1 .. 2^24; the 2 s limit of
+ * every device wait also applies).  When the wait gives up the kernel records
+ * PBIT_ETIMEOUT in a device status word and returns, as the pass does; the
+ * call reads the word back.  Expected result: PBIT_ETIMEOUT, with the CUDA
+ * context still usable.  PBIT_EINVAL: `iterations` out of range (checked
+ * before any CUDA call); PBIT_ECUDA: a CUDA call failed.  Allocates and frees
+ * 4 bytes of device memory; synchronizes `stream` (a cudaStream_t, NULL = the
+ * legacy default stream).
+ */
+pbit_status pbit_selftest_bounded_wait(int64_t iterations, void *stream);
+
+/*
  * Per-kernel device timing (instrumentation; not part of the method).  While
  * enabled on a thread, every sort call on that thread records a CUDA event
  * after each kernel on its stream; pbit_profile_read() then returns, for the

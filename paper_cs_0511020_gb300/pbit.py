@@ -23,7 +23,7 @@ EXPORTS = ("pbit_status_string", "pbit_workspace_size", "pbit_sort_list", "pbit_
            "pbit_serve_poll", "pbit_serve_wait", "pbit_serve_times", "pbit_serve_release", "pbit_serve_stats",
            "pbit_serve_destroy", "pbit_graph_create_batched", "pbit_graph_create_single", "pbit_graph_launch",
            "pbit_graph_result", "pbit_graph_node_count", "pbit_graph_destroy", "pbit_autotune_workspace_size",
-           "pbit_autotune_batched")
+           "pbit_autotune_batched", "pbit_selftest_bounded_wait")
 
 
 class PbitError(RuntimeError):
@@ -113,12 +113,20 @@ def lib():
         L.pbit_autotune_batched.restype = ctypes.c_int
         L.pbit_autotune_batched.argtypes = [vp, i32, vp, vp, i32, i32, vp, vp, ctypes.c_size_t, i32, vp, vp,
                                             ctypes.POINTER(ctypes.c_float)]
+        L.pbit_selftest_bounded_wait.restype = ctypes.c_int
+        L.pbit_selftest_bounded_wait.argtypes = [i64, vp]
         L.pbit_serve_stats.restype = None
         L.pbit_serve_stats.argtypes = [vp, ctypes.POINTER(i64)]
         L.pbit_serve_destroy.restype = None
         L.pbit_serve_destroy.argtypes = [vp]
         _lib = L
     return _lib
+
+
+def selftest_bounded_wait(iterations: int = 1 << 12, stream=None) -> int:
+    """Make a bounded device wait run out on purpose; returns the status the
+    library reports (ETIMEOUT when the wait gave up as designed)."""
+    return int(lib().pbit_selftest_bounded_wait(int(iterations), _stream_handle(stream)))
 
 
 def status_string(st: int) -> str:

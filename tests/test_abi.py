@@ -160,3 +160,5 @@ def test_more_argument_checks_without_a_device(so):
     assert L.pbit_graph_launch(None, None) == pbit.EINVAL
     assert L.pbit_graph_result(None, None, None) == pbit.EINVAL
     assert L.pbit_graph_node_count(None) == 0
+    assert L.pbit_selftest_bounded_wait(0, None) == pbit.EINVAL
+    assert L.pbit_selftest_bounded_wait((1 << 24) + 1, None) == pbit.EINVAL
