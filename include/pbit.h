@@ -164,6 +164,31 @@ pbit_status pbit_sort_list_noalloc(const pbit_pool *pool, int32_t root, int64_t 
 int64_t pbit_last_launch_count(void);
 
 /*
+ * Stage check (testing; not part of the method): runs the single-list
+ * pipeline of pbit_sort_list (always the general path, never the one-kernel
+ * path for short lists) only up to one stage and copies that stage's output
+ * to the caller's device arrays, leaving next[] untouched.
+ *   stage 1: the ranking -- d_idx[r] = the node at position r of the list
+ *            (from the root), d_key[r] = its sort key (for unsigned ascending
+ *            keys: key mod 2^M), the walk the paper's split loop makes along
+ *            L->next (Sec. "Implementation in C++");
+ *   stage 2: the first MSD pass -- the ranked nodes stably partitioned by
+ *            bits [M-4, M) of their sort keys (the library's digit is 4 bits
+ *            wide whatever K is), buckets in ascending digit order: one level
+ *            of the paper's split (Sec. "The idea of sorting using Pbit").
+ *            Only lists of more than 4096 nodes with M above 16 take a global
+ *            pass (smaller ones are finished in shared memory), so stage 2
+ *            refuses others with PBIT_EINVAL.  When bits [M-4, M) are equal in
+ *            every key, the first iteration only moves the list on to its top
+ *            varying bit and d_idx / d_key are unspecified.
+ * d_idx holds n int32; d_key holds n keys of the pool's key width.  Same
+ * argument checks, workspace and errors as pbit_sort_list, plus PBIT_EINVAL
+ * for another stage; synchronizes `stream`.
+ */
+pbit_status pbit_debug_stage(const pbit_pool *pool, int32_t root, int64_t n, int32_t M, int32_t K, int32_t stage,
+                             void *ws, size_t ws_bytes, int32_t *d_idx, void *d_key, void *stream);
+
+/*
  * Self-test of the bounded device wait (failure detection; not part of the
  * method, which has no waits: the paper's sort is sequential).  One CTA
  * waits on a shared-memory mbarrier that nothing ever completes, through the

@@ -145,7 +145,7 @@ Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms) {
     z.R0 = (ncap + S - 1) / S;
     z.Rcap = z.R0 + L;
     // slack: every walk warp may hold one partly used super-chunk of 64 chunks
-    // (grid as launch_walk sizes it)
+    // (for the largest grid launch_walk uses: 8 CTAs of 8 warps per SM)
     const int64_t walk_blocks = std::min<int64_t>((int64_t)sms * 8, std::max<int64_t>(1, ((z.Rcap + 31) / 32 + 7) / 8));
     const int64_t walk_warps = walk_blocks * 8;
     z.chunk_cap = (ncap + z.CH - 1) / z.CH + z.Rcap + 64 * walk_warps + 64;
@@ -265,7 +265,7 @@ static int ceil_log2(int64_t x) {
 // Enqueue the whole sort on stream s.  Returns PBIT_ECUDA if a launch failed.
 pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const ListDesc *tmpl,
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s,
-                         int sms, int64_t *launches, bool small_lists) {
+                         int sms, int64_t *launches, bool small_lists, int stop_after) {
     int64_t n = 0;  // kernel launches
     prof_begin(s);
     if (ms.count < 0)
@@ -298,11 +298,16 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     const int rounds = ceil_log2(cc.Scap) + 1;  // pointer jumping over the ruler walks
     launch_wyllie(cc, s, sms, rounds);
     launch_validate_emit(cc, s, sms);
+    if (stop_after == 1)
+        return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
     launch_plan_init(cc, s);
     n += 8 + rounds;
     const int iters = (M + cc.D - 1) / cc.D;
-    for (int it = 0; it < iters; ++it)
+    for (int it = 0; it < iters; ++it) {
         launch_iteration(cc, it, s, sms);
+        if (stop_after == 2)
+            return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
+    }
     n += iters * launches_per_iteration();
     launch_check_done(cc, iters, s);
     launch_finish_relink(cc, s, sms);
@@ -375,7 +380,7 @@ ListDesc pool_template(const pbit_pool *p) {
 pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
                                 const int64_t *d_offsets, int single_root, int64_t single_n, int M,
                                 int32_t *d_new_roots, const pbit_tune *tune, void *ws, size_t ws_bytes,
-                                cudaStream_t s, Ctx *out) {
+                                cudaStream_t s, Ctx *out, int stop_after) {
     Tune t;
     if (!resolve_tune(tune, pool->pool_size, pool->key_type, &t))
         return PBIT_EINVAL;
@@ -407,7 +412,7 @@ pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t
     ListDesc tmpl = pool_template(pool);
     pbit_status rc;
     if (d_offsets) {
-        rc = enqueue_sort(c, ms, 0, &tmpl, d_offsets, d_roots, M, s, sms, &g_last_launches);
+        rc = enqueue_sort(c, ms, 0, &tmpl, d_offsets, d_roots, M, s, sms, &g_last_launches, false, stop_after);
     } else {
         // single list: its descriptor comes from the call arguments
         ListDesc d = tmpl;
@@ -415,7 +420,8 @@ pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t
         d.root = single_root;
         d.id_base = 0;
         d.out_base = 0;
-        rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, &g_last_launches, single_n <= kSmallList);
+        rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, &g_last_launches,
+                          single_n <= kSmallList && stop_after == 0, stop_after);
     }
     *out = c;
     return rc;
@@ -530,6 +536,28 @@ pbit_status pbit_sort_list(const pbit_pool *pool, int32_t root, int64_t n, int32
         return PBIT_EBADLIST;
     return sort_pool(pool, 1, nullptr, nullptr, root, n, M, nullptr, new_root_host, tune, ws, ws_bytes,
                      (cudaStream_t)stream);
+}
+
+pbit_status pbit_debug_stage(const pbit_pool *pool, int32_t root, int64_t n, int32_t M, int32_t K, int32_t stage,
+                             void *ws, size_t ws_bytes, int32_t *d_idx, void *d_key, void *stream) {
+    if (!check_pool(pool, M, K) || n != pool->pool_size || n < 1 || (stage != 1 && stage != 2) || !d_idx || !d_key)
+        return PBIT_EINVAL;
+    if (stage == 2 && (n <= kSmallList || M <= kMidSpan))
+        return PBIT_EINVAL;  // no global pass would run
+    if (root < 0 || root >= n)
+        return PBIT_EBADLIST;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx c;
+    const pbit_status rc = enqueue_pool(pool, 1, nullptr, nullptr, root, n, M, nullptr, nullptr, ws, ws_bytes, s, &c,
+                                        stage);
+    if (rc != PBIT_OK)
+        return rc;
+    const int b = stage == 1 ? 0 : 1;  // the ranking fills buffer 0, the first pass writes buffer 1
+    if (cudaMemcpyAsync(d_idx, c.idxb[b], 4 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_key, c.keyb[b], (size_t)pool->key_type * (size_t)n, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess)
+        return PBIT_ECUDA;
+    return finish_call(c, nullptr, s);
 }
 
 pbit_status pbit_sort_lists_batched(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,

@@ -55,9 +55,11 @@ Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms);
 size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms);
 // small_lists: every list has at most kSmallList nodes (known on the host):
 // one kernel sorts each list in shared memory instead of the whole pipeline.
+// stop_after: 0 = the whole sort; 1 = stop after the ranking (list order in
+// buffer 0); 2 = stop after the first MSD iteration (its output in buffer 1).
 pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const ListDesc *tmpl,
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s, int sms,
-                         int64_t *launches, bool small_lists = false);
+                         int64_t *launches, bool small_lists = false, int stop_after = 0);
 pbit_status map_status(int st);
 bool check_pool(const pbit_pool *p, int M, int K);
 bool prof_set(bool on);  // per-thread event profiling on/off; returns the previous state
@@ -68,7 +70,7 @@ ListDesc pool_template(const pbit_pool *p);
 pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
                          const int64_t *d_offsets, int single_root, int64_t single_n, int M,
                          int32_t *d_new_roots, const pbit_tune *tune, void *ws, size_t ws_bytes,
-                         cudaStream_t s, Ctx *out);
+                         cudaStream_t s, Ctx *out, int stop_after = 0);
 
 // Byte ranges of a pool: the next[] region, and the key[] / prev[] regions
 // when they do not lie inside it (AoS keeps the key inside the node).

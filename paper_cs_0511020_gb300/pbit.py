@@ -23,7 +23,7 @@ EXPORTS = ("pbit_status_string", "pbit_workspace_size", "pbit_sort_list", "pbit_
            "pbit_serve_poll", "pbit_serve_wait", "pbit_serve_times", "pbit_serve_release", "pbit_serve_stats",
            "pbit_serve_destroy", "pbit_graph_create_batched", "pbit_graph_create_single", "pbit_graph_launch",
            "pbit_graph_result", "pbit_graph_node_count", "pbit_graph_destroy", "pbit_autotune_workspace_size",
-           "pbit_autotune_batched", "pbit_selftest_bounded_wait")
+           "pbit_autotune_batched", "pbit_selftest_bounded_wait", "pbit_debug_stage")
 
 
 class PbitError(RuntimeError):
@@ -113,6 +113,8 @@ def lib():
         L.pbit_autotune_batched.restype = ctypes.c_int
         L.pbit_autotune_batched.argtypes = [vp, i32, vp, vp, i32, i32, vp, vp, ctypes.c_size_t, i32, vp, vp,
                                             ctypes.POINTER(ctypes.c_float)]
+        L.pbit_debug_stage.restype = ctypes.c_int
+        L.pbit_debug_stage.argtypes = [vp, i32, i64, i32, i32, i32, vp, ctypes.c_size_t, vp, vp, vp]
         L.pbit_selftest_bounded_wait.restype = ctypes.c_int
         L.pbit_selftest_bounded_wait.argtypes = [i64, vp]
         L.pbit_serve_stats.restype = None
@@ -121,6 +123,19 @@ def lib():
         L.pbit_serve_destroy.argtypes = [vp]
         _lib = L
     return _lib
+
+
+def debug_stage(pool: Pool, root: int, n: int, M: int, stage: int, K: int = 4, ws=None, stream=None):
+    """(status, idx, key) after the ranking (stage 1) or the first MSD pass
+    (stage 2) of the single-list pipeline; idx and key are new device tensors."""
+    if ws is None:
+        ws = alloc_workspace(workspace_size(n, 1, pool.key_type))
+    idx = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    key = torch.empty(max(n, 1) * pool.key_type, dtype=torch.uint8, device="cuda")
+    st = lib().pbit_debug_stage(ctypes.addressof(pool), int(root), int(n), int(M), int(K), int(stage),
+                                ws.data_ptr(), ws.numel() * ws.element_size(), idx.data_ptr(), key.data_ptr(),
+                                _stream_handle(stream))
+    return int(st), idx[:n], key[:n * pool.key_type]
 
 
 def selftest_bounded_wait(iterations: int = 1 << 12, stream=None) -> int:
