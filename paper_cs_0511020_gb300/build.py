@@ -2,7 +2,7 @@
 
 Each translation unit under csrc/ is compiled by nvcc in parallel, then linked
 into paper_cs_0511020_gb300/_build/libpbit.so (CUDA runtime linked
-statically, so the library needs only the driver).
+statically, so the library needs only the NVIDIA driver).
 """
 from __future__ import annotations
 
