@@ -160,5 +160,12 @@ def test_more_argument_checks_without_a_device(so):
     assert L.pbit_graph_launch(None, None) == pbit.EINVAL
     assert L.pbit_graph_result(None, None, None) == pbit.EINVAL
     assert L.pbit_graph_node_count(None) == 0
+    out = ctypes.c_void_p(0x4000)
+    for stage in (0, 3):
+        assert L.pbit_debug_stage(ctypes.addressof(pool), 0, 100, 32, 4, stage, None, 0, out, out, None) == pbit.EINVAL
+    # stage 2 needs a list long enough for a global pass
+    assert L.pbit_debug_stage(ctypes.addressof(pool), 0, 100, 32, 4, 2, None, 0, out, out, None) == pbit.EINVAL
+    assert L.pbit_debug_stage(ctypes.addressof(pool), 0, 100, 32, 4, 1, None, 0, None, out, None) == pbit.EINVAL
+    assert L.pbit_debug_stage(ctypes.addressof(pool), 100, 100, 32, 4, 1, None, 0, out, out, None) == pbit.EBADLIST
     assert L.pbit_selftest_bounded_wait(0, None) == pbit.EINVAL
     assert L.pbit_selftest_bounded_wait((1 << 24) + 1, None) == pbit.EINVAL
