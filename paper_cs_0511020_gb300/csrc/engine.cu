@@ -20,6 +20,8 @@
 #include <mutex>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "engine.h"
 #include "pbit_internal.cuh"
 
@@ -82,6 +84,15 @@ static void prof_begin(cudaStream_t s) {
 }
 
 static inline size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// NVTX range over a scope: a profiler attached to the process shows when each
+// stage's launches were enqueued (no cost without one).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 int device_sms() {
     int dev = 0;
@@ -266,6 +277,7 @@ static int ceil_log2(int64_t x) {
 pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const ListDesc *tmpl,
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s,
                          int sms, int64_t *launches, bool small_lists, int stop_after) {
+    NvtxRange whole("pbit_sort");
     int64_t n = 0;  // kernel launches
     prof_begin(s);
     if (ms.count < 0)
@@ -280,6 +292,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     cc.M = M;
     launch_setup(cc, d_offsets, d_roots, mode, tmpl, s, sms);
     if (small_lists && mode != 0) {
+        NvtxRange r("pbit_short_lists");
         launch_small(cc, s, sms);
         if (g_prof.on) {
             g_prof.kb = cc.key_bytes;
@@ -291,26 +304,35 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     }
     if (g_prof.on)
         g_prof.small = false;
-    launch_pack(cc, s, sms);
-    if (cc.pack)
-        ++n;
-    launch_walk(cc, s, sms);
     const int rounds = ceil_log2(cc.Scap) + 1;  // pointer jumping over the ruler walks
-    launch_wyllie(cc, s, sms, rounds);
-    launch_validate_emit(cc, s, sms);
+    {
+        NvtxRange r("pbit_rank");
+        launch_pack(cc, s, sms);
+        if (cc.pack)
+            ++n;
+        launch_walk(cc, s, sms);
+        launch_wyllie(cc, s, sms, rounds);
+        launch_validate_emit(cc, s, sms);
+    }
     if (stop_after == 1)
         return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
-    launch_plan_init(cc, s);
     n += 8 + rounds;
     const int iters = (M + cc.D - 1) / cc.D;
-    for (int it = 0; it < iters; ++it) {
-        launch_iteration(cc, it, s, sms);
-        if (stop_after == 2)
-            return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
+    {
+        NvtxRange r("pbit_msd_passes");
+        launch_plan_init(cc, s);
+        for (int it = 0; it < iters; ++it) {
+            launch_iteration(cc, it, s, sms);
+            if (stop_after == 2)
+                return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
+        }
     }
     n += iters * launches_per_iteration();
-    launch_check_done(cc, iters, s);
-    launch_finish_relink(cc, s, sms);
+    {
+        NvtxRange r("pbit_finish_relink");
+        launch_check_done(cc, iters, s);
+        launch_finish_relink(cc, s, sms);
+    }
     n += 4;
     if (g_prof.on) {
         g_prof.rcap = cc.Rcap;
