@@ -141,12 +141,21 @@ pbit_status pbit_sort_list_host(const pbit_pool *host_pool, int32_t root, int64_
  * workspace).  The paper has no counterpart: this is a library convenience.
  *   - The scratch space is a fixed 8 MiB array in the library's device
  *     image; every GPU that loads the library holds it until the process
- *     exits.  Lists longer than 65536 nodes are rejected with PBIT_ENOMEM.
+ *     exits.  Lists longer than 65536 nodes are rejected with PBIT_ENOMEM
+ *     (nothing is written).
  *   - The call allocates nothing: no device memory, no pinned host memory,
- *     no CUDA event or stream (per-kernel profiling is suspended for it).
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on that device.
+ *     no CUDA event or stream.  It records no per-kernel profile
+ *     (pbit_profile_read returns no entries after it); pbit_last_launch_count
+ *     counts its launches.
+ *   - Warm-up: the CUDA runtime loads kernels and the scratch array onto a
+ *     device lazily, at their first use, and that load takes device memory.
+ *     The first call on a device also looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current.  So make one call per
+ *     key type on each device (a tiny list will do) before the caller's
+ *     allocator reserves the device's memory and before any stream capture on
+ *     that device; from then on the calls take no device memory.  (Setting
+ *     CUDA_MODULE_LOADING=EAGER in the environment loads every kernel when the
+ *     process starts instead.)
  *   - All calls share the one array, which keeps the last call's contents;
  *     each call clears what it needs cleared.  Calls whose GPU work overlaps
  *     (other threads, other streams) race on the array: serialize them.

@@ -16,6 +16,14 @@ algorithms" (D. S. Planeta):
   concatenation of Sec. 5.1 written as ``next[s[i]] = s[i+1]``.  The paper
   claims stability (abstract, Sec. 3); numpy's stable argsort is the library
   primitive used as the sort step.
+* ``float_order_keys`` -- the order of IEEE-754 keys (Sec. "Floating-point
+  numbers sorting"): the paper sorts by mantissa and then stably by
+  characteristic, which orders non-negative values but ignores the sign.  The
+  reading taken here extends it to every bit pattern with the totalOrder
+  relation of IEEE 754-2008 (Sec. 5.10): -NaN < -inf < negative numbers < -0
+  < +0 < positive numbers < +inf < +NaN, NaNs of one sign ordered by their
+  payload (a quiet NaN beyond a signaling one).  It is written from the
+  decoded sign, exponent and fraction fields.
 * ``check_sorted_list`` -- properties that pin the result at any size:
   the output list is a permutation of the input list, keys are
   non-decreasing along it, and equal keys keep their input list order.  These
@@ -138,6 +146,33 @@ def sort_key(key: np.ndarray, M: int, signed: bool = False) -> np.ndarray:
     return u
 
 
+_FLOAT_FIELDS = {4: (np.uint32, np.float32, 23, 8), 8: (np.uint64, np.float64, 52, 11)}
+
+
+def float_order_keys(key: np.ndarray):
+    """Three arrays (cls, val, zero_rank) whose lexicographic order is the
+    IEEE 754 totalOrder of the binary32 / binary64 values whose bit patterns
+    are ``key``: cls 0 = NaN with the sign set, 1 = a number or an infinity,
+    2 = NaN without the sign; val = the NaN's fraction field (negated for a
+    negative NaN: a larger payload lies further out) or the value itself;
+    zero_rank orders -0 before +0, the only distinct patterns of equal value."""
+    k = np.ascontiguousarray(key)
+    utype, ftype, fbits, ebits = _FLOAT_FIELDS[k.itemsize]
+    u = k.view(utype)
+    sign = (u >> utype(fbits + ebits)) & utype(1)
+    expo = (u >> utype(fbits)) & utype((1 << ebits) - 1)
+    frac = u & utype((1 << fbits) - 1)
+    is_nan = (expo == utype((1 << ebits) - 1)) & (frac != 0)
+    with np.errstate(invalid="ignore"):  # NaN patterns are not used as values
+        value = k.view(ftype).astype(np.float64)  # exact: binary32 widens without rounding
+    frac_f = frac.astype(np.float64)  # exact: at most 52 bits
+    neg = sign == 1
+    cls = np.where(is_nan, np.where(neg, 0, 2), 1).astype(np.int8)
+    val = np.where(is_nan, np.where(neg, -frac_f, frac_f), value)
+    zero_rank = np.where(neg, 0, 1).astype(np.int8)
+    return cls, val, zero_rank
+
+
 def relink(next_idx: np.ndarray, sorted_nodes: np.ndarray):
     """Concatenate the sorted fragments: next[s[i]] = s[i+1], last -> -1."""
     out = np.array(next_idx, dtype=np.int32, copy=True)
@@ -149,9 +184,19 @@ def relink(next_idx: np.ndarray, sorted_nodes: np.ndarray):
 
 
 def stable_sort_definition(next_idx: np.ndarray, key: np.ndarray, root: int, M: int,
-                           signed: bool = False, descending: bool = False):
-    """(next_out, new_root) of a stable sort of the list by its key."""
+                           signed: bool = False, descending: bool = False, float_keys: bool = False):
+    """(next_out, new_root) of a stable sort of the list by its key
+    (``float_keys``: by the IEEE order of ``float_order_keys``)."""
     order = list_order(next_idx, root)
+    if float_keys:
+        assert M == 8 * key.itemsize and key.itemsize in (4, 8)
+        cls, val, zr = float_order_keys(key[order])
+        pos = np.arange(order.size)
+        if descending:  # largest first, equal patterns still in list order
+            perm = np.lexsort((pos, -zr.astype(np.int16), -val, -cls.astype(np.int16)))
+        else:
+            perm = np.lexsort((pos, zr, val, cls))
+        return relink(next_idx, order[perm])
     sk = sort_key(key, M, signed)[order]
     if descending:
         # stable descending: reverse a stable ascending sort of the reversed list

@@ -13,11 +13,12 @@
  *   - the split loop: walk the list once, push each node onto the front of
  *     the bucket selected by the K-bit digit (data >> M) & (Omega-1), after
  *     M has been decreased by K                 Sec. "Implementation in C++", Sec. "Cutting bits off"
- *   - recursion into every bucket while M > 0, otherwise concatenation of the
- *     leaf buckets with merge(A, B)             Sec. "Implementation in C++", Sec. 5.1 "Function merge"
- *   - ascending order: buckets visited from Omega-1 down to 0, each result
- *     becoming the "end marker" P of the next  Sec. "Differences between sorting in descending and ascending order"
- *   - descending order: buckets visited 0 .. Omega-1 (same section)
+ *   - every bucket sorted the same way on the bits left while any are left,
+ *     then the leaf buckets concatenated with merge(A, B)
+ *                                               Sec. "Implementation in C++", Sec. 5.1 "Function merge"
+ *   - ascending order: the output assembled from its far end, bucket Omega-1
+ *     first, each lower bucket hung in front  Sec. "Differences between sorting in descending and ascending order"
+ *   - descending order: bucket 0 first (same section)
  *   - signed keys: split into negatives and non-negatives by pushing onto two
  *     lists, sort both, concatenate           Sec. "Negative numbers sorting", Sec. "Complete Pbit implementation"
  *   - the merge-step counter (always n) and the split counter (n*M/K)
@@ -32,8 +33,10 @@
  *     number of reversals (M/K, plus one for the signed split) is even.  The
  *     oracle reproduces the literal code exactly; the stable-sort definition
  *     used for the other cases lives in oracle.py.
- *   - bucket tables are taken from the heap instead of the stack so that K up
- *     to 16 (Omega = 65536) does not exhaust the thread stack.
+ *   - the recursion is carried out with an explicit stack of lists still to
+ *     be sorted (same visiting order), and the bucket table comes from the
+ *     heap, so K up to 16 (Omega = 65536) and M up to 64 need no deep call
+ *     stack.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -69,36 +72,102 @@ static onode *omerge(onode *A, onode *B, ostate *st)
     return A;
 }
 
-/* One recursive Pbit call on list L with M unsorted top bits and end marker P. */
-static onode *opbit(onode *L, unsigned M, onode *P, ostate *st, uint64_t level)
+/*
+ * Work that is still to be done: a list whose low `bits` bits are not yet
+ * sorted (bits == 0: a finished leaf bucket, ready to be concatenated).
+ */
+typedef struct {
+    onode *list;
+    unsigned bits;
+    uint64_t level;
+} owork;
+
+typedef struct {
+    owork *item;
+    size_t count, cap;
+} ostack;
+
+static int ostack_push(ostack *s, onode *list, unsigned bits, uint64_t level)
 {
-    if (L == NULL)
-        return P;
-    if (level > st->depth)
-        st->depth = level;
-    M -= st->K;
-    onode **tab = (onode **)calloc((size_t)st->omega, sizeof(onode *));
-    if (tab == NULL) {
+    if (s->count == s->cap) {
+        size_t cap = s->cap ? 2 * s->cap : 256;
+        owork *p = (owork *)realloc(s->item, cap * sizeof(owork));
+        if (p == NULL)
+            return 0;
+        s->item = p;
+        s->cap = cap;
+    }
+    s->item[s->count].list = list;
+    s->item[s->count].bits = bits;
+    s->item[s->count].level = level;
+    s->count++;
+    return 1;
+}
+
+/*
+ * Sort list L on its low M bits and put the result in front of the list P
+ * (the paper's third argument, the part of the output already built behind
+ * it); returns the head of the combined list.
+ *
+ * The method (Sec. "The idea of sorting using Pbit", Sec. "Implementation in
+ * C++"): take the K bits just below the bits already used (M is lowered by K
+ * before the shift), and distribute the nodes over Omega = 2^K buckets by
+ * that digit, each node going to the FRONT of its bucket; then sort every
+ * bucket on the remaining bits the same way; a bucket with no bits left is a
+ * finished piece and is concatenated with merge(A, B) (Sec. 5.1).  The output
+ * is assembled from its far end: for ascending order the highest bucket is
+ * finished first and each lower one is hung in front of it (Sec.
+ * "Differences between sorting in descending and ascending order"; for
+ * descending order bucket 0 is finished first).
+ *
+ * Instead of recursing, the lists still to be handled wait on an explicit
+ * stack; the buckets of one split are pushed so that the one to be finished
+ * first is on top, which visits them in the same order as the recursion.
+ */
+static onode *opbit(onode *L, unsigned M, onode *P, ostate *st)
+{
+    ostack todo = {NULL, 0, 0};
+    onode **bucket = (onode **)malloc((size_t)st->omega * sizeof(onode *));
+    if (bucket == NULL || !ostack_push(&todo, L, M, 1)) {
         st->oom = 1;
+        free(bucket);
+        free(todo.item);
         return P;
     }
-    /* split: every node goes to the front of the bucket named by its digit */
-    while (L) {
-        onode *i = L;
-        onode **in = tab + ((L->data >> M) & (st->omega - 1));
-        L = L->next;
-        i->next = *in;
-        *in = i;
-        st->splits++;
+    while (todo.count > 0) {
+        owork w = todo.item[--todo.count];
+        if (w.list == NULL)
+            continue;
+        if (w.bits == 0) {  /* a leaf bucket: concatenate it in front of P */
+            P = omerge(w.list, P, st);
+            continue;
+        }
+        if (w.level > st->depth)
+            st->depth = w.level;
+        const unsigned rest = w.bits - st->K;  /* bits left after this digit */
+        memset(bucket, 0, (size_t)st->omega * sizeof(onode *));
+        onode *node = w.list;
+        while (node != NULL) {
+            onode *following = node->next;
+            const uint64_t digit = (node->data >> rest) & (st->omega - 1);
+            node->next = bucket[digit];  /* to the front of its bucket */
+            bucket[digit] = node;
+            st->splits++;
+            node = following;
+        }
+        /* the bucket finished first goes on the stack last */
+        for (uint64_t j = 0; j < st->omega; ++j) {
+            const uint64_t b = st->descending ? st->omega - 1 - j : j;
+            if (!ostack_push(&todo, bucket[b], rest, w.level + 1)) {
+                st->oom = 1;
+                free(bucket);
+                free(todo.item);
+                return P;
+            }
+        }
     }
-    if (!st->descending) {
-        for (int64_t b = (int64_t)st->omega - 1; b >= 0; --b)
-            P = M ? opbit(tab[b], M, P, st, level + 1) : omerge(tab[b], P, st);
-    } else {
-        for (int64_t b = 0; b < (int64_t)st->omega; ++b)
-            P = M ? opbit(tab[b], M, P, st, level + 1) : omerge(tab[b], P, st);
-    }
-    free(tab);
+    free(bucket);
+    free(todo.item);
     return P;
 }
 
@@ -184,7 +253,7 @@ int pbit_oracle_sort(int64_t pool_size, const int32_t *next_in, int64_t next_str
     st.descending = descending;
     onode *P;
     if (!is_signed) {
-        P = opbit(L, (unsigned)M, NULL, &st, 1);
+        P = opbit(L, (unsigned)M, NULL, &st);
     } else {
         /* sign split of the complete implementation: two push-built lists */
         uint64_t sign = (uint64_t)1 << (M - 1);
@@ -201,9 +270,9 @@ int pbit_oracle_sort(int64_t pool_size, const int32_t *next_in, int64_t next_str
             }
         }
         if (!descending)
-            P = opbit(neg, (unsigned)M, opbit(nonneg, (unsigned)M, NULL, &st, 1), &st, 1);
+            P = opbit(neg, (unsigned)M, opbit(nonneg, (unsigned)M, NULL, &st), &st);
         else
-            P = opbit(nonneg, (unsigned)M, opbit(neg, (unsigned)M, NULL, &st, 1), &st, 1);
+            P = opbit(nonneg, (unsigned)M, opbit(neg, (unsigned)M, NULL, &st), &st);
     }
     int rc = st.oom ? -3 : 0;
     if (rc == 0) {

@@ -72,6 +72,15 @@ bool prof_set(bool on) {
     return was;
 }
 
+void prof_forget() {
+    g_prof.marks.clear();
+    g_prof.used = 0;
+    g_prof.start = nullptr;
+    g_prof.have_ctr = false;
+}
+
+int64_t *last_launches_slot() { return &g_last_launches; }
+
 static void prof_begin(cudaStream_t s) {
     if (!g_prof.on)
         return;
@@ -257,8 +266,6 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     x.plan_mid = (int32_t *)take(4 * (size_t)z.seg_cap);
     x.fin = (Fin *)take(sizeof(Fin) * (size_t)z.fin_cap);
     x.mid = (Fin *)take(sizeof(Fin) * (size_t)z.mid_cap);
-    x.lb = (unsigned long long *)take(8 * (size_t)z.tile_cap * bins);
-    zero(x.lb, 0, 8 * (size_t)z.tile_cap * bins);
     x.rel_cursor = (int32_t *)take(4 * (size_t)relink_max_buckets());
     zero(x.rel_cursor, 0, 4 * (size_t)relink_max_buckets());
     if (c)

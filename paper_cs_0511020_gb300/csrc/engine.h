@@ -63,6 +63,11 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
 pbit_status map_status(int st);
 bool check_pool(const pbit_pool *p, int M, int K);
 bool prof_set(bool on);  // per-thread event profiling on/off; returns the previous state
+// Drop this thread's recorded profile, so pbit_profile_read reports nothing
+// until the next profiled call.
+void prof_forget();
+// This thread's launch count of its last sort call (pbit_last_launch_count).
+int64_t *last_launches_slot();
 ListDesc pool_template(const pbit_pool *p);
 
 // Enqueue a sort of a pool with list ranges (d_offsets) or of one list

@@ -95,8 +95,12 @@ extern "C" pbit_status pbit_sort_list_noalloc(const pbit_pool *pool, int32_t roo
     d.id_base = 0;
     d.out_base = 0;
     cudaStream_t s = (cudaStream_t)stream;
-    const bool prof = prof_set(false);  // no timing events (creating them allocates)
-    rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, nullptr, n <= kSmallList);
+    // No timing events (creating them allocates): this call records no
+    // per-kernel profile, and the profile of an earlier call is dropped so it
+    // is not mistaken for this one.
+    const bool prof = prof_set(false);
+    prof_forget();
+    rc = enqueue_sort(c, ms, 2, &d, nullptr, nullptr, M, s, sms, last_launches_slot(), n <= kSmallList);
     prof_set(prof);
     if (rc != PBIT_OK)
         return rc;

@@ -160,7 +160,6 @@ struct Ctx {
     Fin *fin;
     Fin *mid;                   // mid_cap buckets of (cutoff, kMidCap] nodes: one CTA each
     int64_t mid_cap;
-    unsigned long long *lb;     // tile_cap x 16 look-back words
     int32_t *rel_cursor;        // blocked relink: pairs per node block
     int32_t *new_roots;
 };
@@ -345,24 +344,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
             return false;
     }
     return false;
-}
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-// Decoupled look-back words: [63:56] pass epoch, [55:54] state, [53:0] count.
-constexpr unsigned long long kLbAgg = 1ull;
-constexpr unsigned long long kLbIncl = 2ull;
-__device__ __forceinline__ unsigned long long lb_pack(uint32_t epoch, unsigned long long state,
-                                                      unsigned long long count) {
-    return ((unsigned long long)(epoch & 0xff) << 56) | (state << 54) | (count & ((1ull << 54) - 1));
 }
 
 // ---------------------------------------------------------- launch helpers

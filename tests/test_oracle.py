@@ -285,3 +285,108 @@ def test_check_sorted_list_catches_planted_mistakes():
     bad, br = O.relink(nxt, np.array(order[:-1], dtype=np.int32))
     with pytest.raises(AssertionError):
         O.check_sorted_list(nxt, root, bad, br, keys, 16)
+
+
+# ------------------------------------------------------------- float keys
+# Sec. "Floating-point numbers sorting": the paper sorts floats by mantissa and
+# then stably by characteristic.  The oracle's reading (IEEE 754 totalOrder,
+# written from the decoded fields) is pinned three ways: an example whose
+# order is worked out by hand from the IEEE definition, Python's ``sorted``
+# on values decoded by ``struct``, and the paper's own two-step recipe, which
+# is right for non-negative values.
+import struct  # noqa: E402
+
+_F32 = {"+1": 0x3F800000, "-0": 0x80000000, "+qnan": 0x7FC00000, "-inf": 0xFF800000, "+0": 0x00000000,
+        "-snan1": 0xFF800001, "+sub": 0x00000001, "-1.5": 0xBFC00000, "+inf": 0x7F800000,
+        "-qnan": 0xFFC00000, "+2": 0x40000000, "-sub": 0x80000001, "+snan1": 0x7F800001,
+        "+max": 0x7F7FFFFF, "-qnan5": 0xFFC00005}
+_F64 = {"+1": 0x3FF0000000000000, "-0": 0x8000000000000000, "+qnan": 0x7FF8000000000000,
+        "-inf": 0xFFF0000000000000, "+0": 0, "-snan1": 0xFFF0000000000001, "+sub": 1,
+        "-1.5": 0xBFF8000000000000, "+inf": 0x7FF0000000000000, "-qnan": 0xFFF8000000000000,
+        "+2": 0x4000000000000000, "-sub": 0x8000000000000001, "+snan1": 0x7FF0000000000001,
+        "+max": 0x7FEFFFFFFFFFFFFF, "-qnan5": 0xFFF8000000000005}
+# list order of the example (two equal +1 patterns: they must keep this order)
+_EXAMPLE = ["+1", "-0", "+qnan", "-inf", "+0", "-snan1", "+sub", "-1.5", "+inf", "-qnan", "+2", "-sub",
+            "+snan1", "+1", "+max", "-qnan5"]
+# ascending totalOrder worked out by hand: NaNs with the sign set first (a
+# quiet NaN, whose top fraction bit is set, before a signaling one; a larger
+# payload further out), then -inf, the negative numbers, -0, +0, the positive
+# numbers, +inf, and the positive NaNs (signaling before quiet)
+_EXAMPLE_SORTED = [15, 9, 5, 3, 7, 11, 1, 4, 6, 0, 13, 10, 14, 8, 12, 2]
+
+
+@pytest.mark.parametrize("width", [4, 8])
+def test_float_order_hand_example(width):
+    pat = _F32 if width == 4 else _F64
+    dt = np.uint32 if width == 4 else np.uint64
+    key = np.array([pat[name] for name in _EXAMPLE], dtype=dt)
+    nxt, root = I.list_from_order(np.arange(key.size))
+    out, r = O.stable_sort_definition(nxt, key, root, 8 * width, float_keys=True)
+    assert _walk(out, r) == _EXAMPLE_SORTED
+    out, r = O.stable_sort_definition(nxt, key, root, 8 * width, float_keys=True, descending=True)
+    want = list(reversed(_EXAMPLE_SORTED))
+    i, j = want.index(13), want.index(0)  # equal patterns keep list order in both directions
+    want[i], want[j] = want[j], want[i]
+    assert _walk(out, r) == want
+
+
+def _decode(key, width):
+    fmt = "<f" if width == 4 else "<d"
+    return [struct.unpack(fmt, int(k).to_bytes(width, "little"))[0] for k in key]
+
+
+def _finite_and_inf(n, width, seed):
+    g = np.random.default_rng(seed)
+    dt, ft = (np.uint32, np.float32) if width == 4 else (np.uint64, np.float64)
+    vals = (g.standard_normal(n) * 10.0 ** g.integers(-30, 30, n)).astype(ft)
+    key = vals.view(dt).copy()
+    tiny = g.integers(1, 1000, n).astype(dt)  # subnormal patterns
+    sign = dt(1) << dt(8 * width - 1)
+    key[::13] = tiny[::13]
+    key[1::17] = tiny[1::17] | sign
+    key[2::19] = 0
+    key[3::23] = sign
+    key[4::29] = np.array(_F32["+inf"] if width == 4 else _F64["+inf"], dtype=dt)
+    key[5::31] = np.array(_F32["-inf"] if width == 4 else _F64["-inf"], dtype=dt)
+    key[6::7] = key[0]  # repeated patterns
+    return key
+
+
+@pytest.mark.parametrize("width", [4, 8])
+def test_float_order_vs_python_sorted(width):
+    n = 5000
+    key = _finite_and_inf(n, width, 701 + width)
+    nxt, root = I.random_list(n, 702)
+    order = _walk(nxt, root)
+    dec = _decode(key, width)
+    # numbers by value; of the two zeros, the one with the sign set first;
+    # Python's sort is stable, so equal patterns keep list order
+    want = sorted(order, key=lambda v: (dec[v], 0 if struct.pack(">d", dec[v])[0] & 0x80 else 1))
+    out, r = O.stable_sort_definition(nxt, key, root, 8 * width, float_keys=True)
+    assert _walk(out, r) == want
+
+
+@pytest.mark.parametrize("width", [4, 8])
+def test_float_order_matches_paper_recipe_on_non_negative_values(width):
+    """The paper's recipe: stable sort by the mantissa (fraction field), then
+    stable sort by the characteristic (exponent field).  For values without
+    the sign bit (zeros, subnormals, normals, +inf) it orders by value."""
+    n = 4000
+    key = _finite_and_inf(n, width, 711 + width)
+    sign = (1 << (8 * width - 1))
+    key = key & key.dtype.type(sign - 1)  # clear the sign bit
+    nxt, root = I.random_list(n, 712)
+    order = _walk(nxt, root)
+    fbits = 23 if width == 4 else 52
+    by_mantissa = sorted(order, key=lambda v: int(key[v]) & ((1 << fbits) - 1))
+    recipe = sorted(by_mantissa, key=lambda v: int(key[v]) >> fbits)
+    out, r = O.stable_sort_definition(nxt, key, root, 8 * width, float_keys=True)
+    assert _walk(out, r) == recipe
+    # with negative values the recipe (which ignores the sign) is not an order
+    # by value, and the oracle's reading departs from it
+    key2 = key.copy()
+    key2[::3] |= key.dtype.type(sign)
+    by_mantissa = sorted(order, key=lambda v: int(key2[v]) & ((1 << fbits) - 1))
+    recipe2 = sorted(by_mantissa, key=lambda v: (int(key2[v]) & (sign - 1)) >> fbits)
+    out2, r2 = O.stable_sort_definition(nxt, key2, root, 8 * width, float_keys=True)
+    assert _walk(out2, r2) != recipe2
