@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--log2n", type=int, default=27, help="list size (27 = the benchmark workload)")
     ap.add_argument("--key-bits", type=int, default=32,
                     help="keys uniform over this many low bits and M = this (32 = the benchmark workload)")
+    ap.add_argument("--digit-bits", type=int, default=0,
+                    help="GPU digit width of the timed sort (0 = the call's K)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2n", type=int, default=24)
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-list batched leg")
@@ -205,12 +207,13 @@ def run_ours(a):
     d_next = d_next0.clone()
     d_key = torch.from_numpy(key.view(np.int32)).cuda()
     pool = pbit.make_pool(d_next, d_key)
-    ws = pbit.alloc_workspace(pbit.workspace_size(n, 1, 4))
+    tune = {"digit_bits": a.digit_bits} if a.digit_bits else None
+    ws = pbit.alloc_workspace(pbit.workspace_size(n, 1, 4, tune))
     stream = torch.cuda.current_stream()
 
     def step():
         d_next.copy_(d_next0)
-        st, r = pbit.sort_pool_list(pool, root, n, M, 4, ws=ws, stream=stream, check=False)
+        st, r = pbit.sort_pool_list(pool, root, n, M, 4, ws=ws, stream=stream, check=False, tune=tune)
         if st != pbit.OK:
             raise pbit.PbitError(st, "bench step")
         return r
@@ -232,7 +235,7 @@ def run_ours(a):
     for i in range(a.steps):
         d_next.copy_(d_next0)
         ev0[i].record(stream)
-        st, _ = pbit.sort_pool_list(pool, root, n, M, 4, ws=ws, stream=stream, check=False)
+        st, _ = pbit.sort_pool_list(pool, root, n, M, 4, ws=ws, stream=stream, check=False, tune=tune)
         ev1[i].record(stream)
         if st != pbit.OK:
             raise pbit.PbitError(st, "bench step")
@@ -263,7 +266,7 @@ def run_ours(a):
     h_next = h_next0.clone().pin_memory()
     h_key = torch.from_numpy(key.view(np.int32)).pin_memory()
     hpool = pbit.host_pool(h_next, h_key)
-    ws_h = pbit.alloc_workspace(pbit.workspace_size_host(hpool))
+    ws_h = pbit.alloc_workspace(pbit.workspace_size_host(hpool, tune))
     del ws
     torch.cuda.empty_cache()
     e2e_times = []
@@ -271,7 +274,7 @@ def run_ours(a):
         h_next.copy_(h_next0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        st, r = pbit.sort_pool_list_host(hpool, root, n, M, 4, ws=ws_h, stream=stream, check=False)
+        st, r = pbit.sort_pool_list_host(hpool, root, n, M, 4, ws=ws_h, stream=stream, check=False, tune=tune)
         dt = time.perf_counter() - t0
         if st != pbit.OK:
             raise pbit.PbitError(st, "bench e2e step")

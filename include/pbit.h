@@ -19,8 +19,10 @@
  *     Strides must be multiples of the element width.
  *   - next[] is relinked IN PLACE; key[] is only read.
  *   - 1 <= K <= 16, K divides M, 1 <= M <= 8 * key width; otherwise
- *     PBIT_EINVAL.  The result does not depend on K (K only fixes the paper's
- *     digit width); the GPU's own digit width is a tuning choice.
+ *     PBIT_EINVAL.  K is the paper's digit width (Sec. "The length of bit
+ *     pattern"): unless the tune sets another, each GPU MSD pass splits on K
+ *     bits (K <= 8) or on half of a K-bit level (K > 8).  The result does not
+ *     depend on K or on the GPU's digit width: only the number of passes does.
  *   - Before anything is written to next[], the list shape is validated (every
  *     index in range, no cycle, exactly n nodes reachable from the root).  On
  *     any error next[] is left untouched and no root is written.
@@ -75,7 +77,11 @@ typedef struct {
 
 /* Tuning knobs; any field <= 0 takes the built-in / autotuned default. */
 typedef struct {
-    int32_t digit_bits;   /* GPU digit width per MSD pass: 4 (16 buckets) only   */
+    int32_t digit_bits;   /* GPU digit width per MSD pass, 1..8 bits (2^bits     */
+                          /* buckets); <= 0: the call's K when K <= 8, else two  */
+                          /* passes of ceil(K/2) bits per K-bit level (K = 16:   */
+                          /* two 8-bit passes).  The result is the same for any */
+                          /* width: it only changes the number of passes         */
     int32_t smem_cutoff;  /* buckets <= this many nodes are finished in smem     */
     int32_t ruler_stride; /* list ranking: one ruler per this many nodes (2^k)   */
     int32_t gather_pack;  /* 0: by size, 1: off, 2: on -- pack {next, key} per   */
@@ -150,8 +156,10 @@ pbit_status pbit_sort_list_host(const pbit_pool *host_pool, int32_t root, int64_
  *   - Warm-up: the CUDA runtime loads kernels and the scratch array onto a
  *     device lazily, at their first use, and that load takes device memory.
  *     The first call on a device also looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current.  So make one call per
- *     key type on each device (a tiny list will do) before the caller's
+ *     (cudaGetSymbolAddress) with that device current.  So, on each device,
+ *     for each key type and K in use, make one call with a list of more than
+ *     4096 nodes and one with a shorter list (the two take different
+ *     kernels) before the caller's
  *     allocator reserves the device's memory and before any stream capture on
  *     that device; from then on the calls take no device memory.  (Setting
  *     CUDA_MODULE_LOADING=EAGER in the environment loads every kernel when the
@@ -182,14 +190,16 @@ int64_t pbit_last_launch_count(void);
  *            keys: key mod 2^M), the walk the paper's split loop makes along
  *            L->next (Sec. "Implementation in C++");
  *   stage 2: the first MSD pass -- the ranked nodes stably partitioned by
- *            bits [M-4, M) of their sort keys (the library's digit is 4 bits
- *            wide whatever K is), buckets in ascending digit order: one level
- *            of the paper's split (Sec. "The idea of sorting using Pbit").
- *            Only lists of more than 4096 nodes with M above 16 take a global
- *            pass (smaller ones are finished in shared memory), so stage 2
- *            refuses others with PBIT_EINVAL.  When bits [M-4, M) are equal in
- *            every key, the first iteration only moves the list on to its top
- *            varying bit and d_idx / d_key are unspecified.
+ *            bits [M-D, M) of their sort keys, D = the GPU digit width the
+ *            call's K gives (K for K <= 8), buckets in ascending digit order:
+ *            one level of the paper's split (Sec. "The idea of sorting using
+ *            Pbit").  The list takes this pass whatever its length (a sort
+ *            would finish short lists and small buckets in shared memory
+ *            instead); a list of one node is refused with PBIT_EINVAL.  When
+ *            bits [M-D, M) are equal in every key, the first iteration only
+ *            moves the list on to its top varying bit, and when M <= D the
+ *            pass writes the final order instead: d_idx / d_key are then
+ *            unspecified.
  * d_idx holds n int32; d_key holds n keys of the pool's key width.  Same
  * argument checks, workspace and errors as pbit_sort_list, plus PBIT_EINVAL
  * for another stage; synchronizes `stream`.
@@ -265,7 +275,8 @@ void pbit_graph_destroy(pbit_graph *g);
 
 /* --------------------------------------------------------------- autotuner
  * Times the sort of the caller's batch under each candidate tune
- * (shared-memory cutoff 128/256/512 x ruler stride 16/32/64/128; `reps`
+ * (digit width 4/8 x shared-memory cutoff 128/256/512 x ruler stride
+ * 16/32/64/128; `reps`
  * timed runs each after one warm-up, median kept) and returns the fastest in
  * *best (and its median time in *best_ms).  Candidates whose workspace
  * exceeds ws_bytes are skipped; pbit_autotune_workspace_size gives room for

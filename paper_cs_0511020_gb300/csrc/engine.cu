@@ -120,9 +120,14 @@ int device_sms() {
     return sms;
 }
 
-bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out) {
+// GPU digit width of a call whose tune does not set one: the paper's K
+// (Sec. "The length of bit pattern"), K bits per pass up to 8, and a level of
+// more than 8 bits as two passes of ceil(K/2) bits (K = 16: two 8-bit passes).
+static int digit_width_for_K(int K) { return K <= max_digit_bits() ? K : (K + 1) / 2; }
+
+bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, int K, Tune *out) {
     Tune r;
-    r.digit_bits = digit_bits();
+    r.digit_bits = K > 0 ? digit_width_for_K(K) : 0;  // 0: not known (workspace size queries)
     r.cutoff = finish_capacity();
     // Ruler stride: denser rulers for smaller pools, so there are enough
     // sub-walks to fill the GPU and the longest one stays short (measured:
@@ -130,8 +135,10 @@ bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out) {
     r.log2S = pool_size <= (1ll << 23) ? 3 : (pool_size <= (1ll << 25) ? 4 : 5);
     r.pack = 0;
     if (t) {
-        if (t->digit_bits > 0 && t->digit_bits != digit_bits())
+        if (t->digit_bits > max_digit_bits())
             return false;
+        if (t->digit_bits > 0)
+            r.digit_bits = t->digit_bits;
         if (t->smem_cutoff > 0) {
             if (t->smem_cutoff > finish_capacity())
                 return false;
@@ -171,7 +178,8 @@ Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms) {
     z.chunk_cap = (ncap + z.CH - 1) / z.CH + z.Rcap + 64 * walk_warps + 64;
     z.seg_cap = ncap / (t.cutoff + 1) + 2;
     const int64_t iters = (8 * kb + t.digit_bits - 1) / t.digit_bits;
-    z.fin_cap = L + (int64_t)(1 << t.digit_bits) * iters * z.seg_cap + 16;
+    // small buckets are disjoint and non-empty: at most one per node
+    z.fin_cap = std::min<int64_t>(L + (int64_t)(1 << t.digit_bits) * iters * z.seg_cap, ncap + L) + 16;
     z.tile_cap = ncap / pass_tile() + z.seg_cap + 2;
     z.mid_cap = ncap / (t.cutoff + 1) + L + 16;  // disjoint buckets of more than cutoff nodes
     // A random gather costs a whole DRAM sector or more: the pack turns the
@@ -208,7 +216,12 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     x.fin_cap = z.fin_cap;
     x.mid_cap = z.mid_cap;
     x.tile_cap = z.tile_cap;
-    const int bins = 1 << z.tune.digit_bits;
+    // 16-bucket passes use 16 counters per row for every window up to 4 bits;
+    // the 256-bucket passes 256, and they need neither a second parity of
+    // rows and histograms (each iteration counts its own tiles afresh) nor
+    // per-bucket AND/OR
+    const bool wide = z.tune.digit_bits > digit_bits();
+    const int bins = wide ? 1 << wide_digit_bits() : 1 << digit_bits();
 
     x.ctr = (Counters *)take(sizeof(Counters));
     zero(x.ctr, 0, sizeof(Counters));
@@ -241,19 +254,25 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     }
     x.F = (int32_t *)take((size_t)z.ncap * 4 + 64);
     x.pack = z.pack ? x.keyb[1] : nullptr;
-    x.row_cap = 2 * (z.ncap / pass_tile()) + 18 * z.seg_cap + 64;
-    x.scan_cap = z.ncap / ((int64_t)pass_tile() * scan_rows()) + z.seg_cap + 2;
+    // rows: the 16-bucket passes hold next-pass rows (tiles + 16 per bucket
+    // list) besides the statistics rows; the 256-bucket passes only one row
+    // per statistics tile of the pending segments (each longer than the cutoff)
+    x.row_cap = wide ? z.ncap / pass_tile() + z.seg_cap + 64 : 2 * (z.ncap / pass_tile()) + 18 * z.seg_cap + 64;
+    // scan chunks: only segments of more than one tile have them
+    x.scan_cap = z.ncap / ((int64_t)pass_tile() * scan_rows()) + std::min<int64_t>(z.seg_cap, z.ncap / pass_tile()) + 2;
     for (int b = 0; b < 2; ++b) {
         x.act[b] = (Seg *)take(sizeof(Seg) * (size_t)z.seg_cap);
-        x.act_hist[b] = (uint32_t *)take(4 * (size_t)z.seg_cap * bins);
+        x.act_hist[b] = (wide && b == 1) ? x.act_hist[0] : (uint32_t *)take(4 * (size_t)z.seg_cap * bins);
         x.act_tile_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
         x.act_chunk_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
         x.act_nrow_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
-        x.tcnt[b] = (uint32_t *)take(4 * (size_t)x.row_cap * bins);
-        x.band[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap * bins);
-        zero(x.band[b], 0xff, 8 * (size_t)z.seg_cap * bins);
-        x.bor[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap * bins);
-        zero(x.bor[b], 0, 8 * (size_t)z.seg_cap * bins);
+        x.tcnt[b] = (wide && b == 1) ? x.tcnt[0] : (uint32_t *)take(4 * (size_t)x.row_cap * bins);
+        if (!wide) {
+            x.band[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap * bins);
+            zero(x.band[b], 0xff, 8 * (size_t)z.seg_cap * bins);
+            x.bor[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap * bins);
+            zero(x.bor[b], 0, 8 * (size_t)z.seg_cap * bins);
+        }
         x.pend[b] = (Seg *)take(sizeof(Seg) * (size_t)z.seg_cap);
         x.pend_tile_base[b] = (int32_t *)take(4 * (size_t)(z.seg_cap + 1));
         x.pand[b] = (unsigned long long *)take(8 * (size_t)z.seg_cap);
@@ -271,6 +290,17 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     if (c)
         *c = x;
     return off + 256;
+}
+
+size_t workspace_bytes(int64_t ncap, int32_t L, int kb, Tune t, int sms) {
+    if (t.digit_bits > 0)
+        return bind(compute_sizes(ncap, L, kb, t, sms), nullptr, nullptr, nullptr);
+    size_t w = 0;  // digit width not known yet (it follows the call's K): room for every width
+    for (int d = 1; d <= max_digit_bits(); ++d) {
+        t.digit_bits = d;
+        w = std::max(w, bind(compute_sizes(ncap, L, kb, t, sms), nullptr, nullptr, nullptr));
+    }
+    return w;
 }
 
 static int ceil_log2(int64_t x) {
@@ -407,11 +437,11 @@ ListDesc pool_template(const pbit_pool *p) {
 
 // Enqueue a sort of a pool with list ranges (d_offsets) or of one list.
 pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
-                                const int64_t *d_offsets, int single_root, int64_t single_n, int M,
+                                const int64_t *d_offsets, int single_root, int64_t single_n, int M, int K,
                                 int32_t *d_new_roots, const pbit_tune *tune, void *ws, size_t ws_bytes,
                                 cudaStream_t s, Ctx *out, int stop_after) {
     Tune t;
-    if (!resolve_tune(tune, pool->pool_size, pool->key_type, &t))
+    if (!resolve_tune(tune, pool->pool_size, pool->key_type, K, &t))
         return PBIT_EINVAL;
     const int sms = device_sms();
     Sizes z = compute_sizes(pool->pool_size, num_lists, pool->key_type, t, sms);
@@ -419,7 +449,7 @@ pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t
     if (!tune && tune_cache_lookup(pool->pool_size, num_lists, pool->key_type, &cached)) {
         // the autotuned choice for this size class, when it fits the workspace
         Tune tc;
-        if (resolve_tune(&cached, pool->pool_size, pool->key_type, &tc)) {
+        if (resolve_tune(&cached, pool->pool_size, pool->key_type, K, &tc)) {
             const Sizes zc = compute_sizes(pool->pool_size, num_lists, pool->key_type, tc, sms);
             if (bind(zc, nullptr, nullptr, nullptr) <= ws_bytes)
                 z = zc;
@@ -433,6 +463,7 @@ pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t
     c.flags = pool->flags;
     c.shared_pool = 1;
     c.desc_next_stride = pool->next_stride_bytes;
+    c.force_pass = stop_after == 2;  // stage check: every list takes a global pass
     if (z.tune.pack == 0 && pool->key_type == 4 && pool->next_stride_bytes == 8 && pool->key_stride_bytes == 8 &&
         (const unsigned char *)pool->key == (const unsigned char *)pool->next + 4)
         c.pack = nullptr;  // {int32 next; uint32 key} nodes are packed already
@@ -480,11 +511,11 @@ static pbit_status finish_call(const Ctx &c, int32_t *host_root, cudaStream_t s)
 }
 
 static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
-                             const int64_t *d_offsets, int single_root, int64_t single_n, int M,
+                             const int64_t *d_offsets, int single_root, int64_t single_n, int M, int K,
                              int32_t *d_new_roots, int32_t *host_root, const pbit_tune *tune, void *ws,
                              size_t ws_bytes, cudaStream_t s) {
     Ctx c;
-    const pbit_status rc = enqueue_pool(pool, num_lists, d_roots, d_offsets, single_root, single_n, M,
+    const pbit_status rc = enqueue_pool(pool, num_lists, d_roots, d_offsets, single_root, single_n, M, K,
                                         d_new_roots, tune, ws, ws_bytes, s, &c);
     if (rc != PBIT_OK)
         return rc;
@@ -535,15 +566,15 @@ pbit_status pbit_workspace_size(int64_t pool_size, int32_t num_lists, int32_t ke
     if (key_type != 1 && key_type != 2 && key_type != 4 && key_type != 8)
         return PBIT_EINVAL;
     Tune t;
-    if (!resolve_tune(tune, pool_size, key_type, &t))
+    if (!resolve_tune(tune, pool_size, key_type, 0, &t))
         return PBIT_EINVAL;
     const int sms = device_sms();
-    size_t w = bind(compute_sizes(pool_size, num_lists, key_type, t, sms), nullptr, nullptr, nullptr);
+    size_t w = workspace_bytes(pool_size, num_lists, key_type, t, sms);
     pbit_tune cached;
     Tune tc;
     if (!tune && tune_cache_lookup(pool_size, num_lists, key_type, &cached) &&
-        resolve_tune(&cached, pool_size, key_type, &tc))  // room for either choice
-        w = std::max(w, bind(compute_sizes(pool_size, num_lists, key_type, tc, sms), nullptr, nullptr, nullptr));
+        resolve_tune(&cached, pool_size, key_type, 0, &tc))  // room for either choice
+        w = std::max(w, workspace_bytes(pool_size, num_lists, key_type, tc, sms));
     *bytes = w;
     return PBIT_OK;
 }
@@ -563,7 +594,7 @@ pbit_status pbit_sort_list(const pbit_pool *pool, int32_t root, int64_t n, int32
     }
     if (root < 0 || root >= n)
         return PBIT_EBADLIST;
-    return sort_pool(pool, 1, nullptr, nullptr, root, n, M, nullptr, new_root_host, tune, ws, ws_bytes,
+    return sort_pool(pool, 1, nullptr, nullptr, root, n, M, K, nullptr, new_root_host, tune, ws, ws_bytes,
                      (cudaStream_t)stream);
 }
 
@@ -571,13 +602,13 @@ pbit_status pbit_debug_stage(const pbit_pool *pool, int32_t root, int64_t n, int
                              void *ws, size_t ws_bytes, int32_t *d_idx, void *d_key, void *stream) {
     if (!check_pool(pool, M, K) || n != pool->pool_size || n < 1 || (stage != 1 && stage != 2) || !d_idx || !d_key)
         return PBIT_EINVAL;
-    if (stage == 2 && (n <= kSmallList || M <= kMidSpan))
-        return PBIT_EINVAL;  // no global pass would run
+    if (stage == 2 && n < 2)
+        return PBIT_EINVAL;  // nothing to split
     if (root < 0 || root >= n)
         return PBIT_EBADLIST;
     cudaStream_t s = (cudaStream_t)stream;
     Ctx c;
-    const pbit_status rc = enqueue_pool(pool, 1, nullptr, nullptr, root, n, M, nullptr, nullptr, ws, ws_bytes, s, &c,
+    const pbit_status rc = enqueue_pool(pool, 1, nullptr, nullptr, root, n, M, K, nullptr, nullptr, ws, ws_bytes, s, &c,
                                         stage);
     if (rc != PBIT_OK)
         return rc;
@@ -594,7 +625,7 @@ pbit_status pbit_sort_lists_batched(const pbit_pool *pool, int32_t num_lists, co
                                     const pbit_tune *tune, void *ws, size_t ws_bytes, void *stream) {
     if (!check_pool(pool, M, K) || num_lists < 1 || !d_roots || !d_offsets || !d_new_roots)
         return PBIT_EINVAL;
-    return sort_pool(pool, num_lists, d_roots, d_offsets, 0, 0, M, d_new_roots, nullptr, tune, ws, ws_bytes,
+    return sort_pool(pool, num_lists, d_roots, d_offsets, 0, 0, M, K, d_new_roots, nullptr, tune, ws, ws_bytes,
                      (cudaStream_t)stream);
 }
 
@@ -716,7 +747,7 @@ pbit_status pbit_sort_list_host(const pbit_pool *host_pool, int32_t root, int64_
         return PBIT_ECUDA;
     Ctx c;
     const size_t rest = ws_bytes - (size_t)(w - (unsigned char *)ws);
-    pbit_status rc = enqueue_pool(&dp, 1, nullptr, nullptr, root, n, M, nullptr, tune, w, rest, s, &c);
+    pbit_status rc = enqueue_pool(&dp, 1, nullptr, nullptr, root, n, M, K, nullptr, tune, w, rest, s, &c);
     if (rc != PBIT_OK)
         return rc;
     // copy back unconditionally: on an error the device copy was not written

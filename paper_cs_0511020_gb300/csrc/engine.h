@@ -13,7 +13,7 @@ namespace pbit {
 constexpr int64_t kPackAutoBytes = 2ll << 20;
 
 struct Tune {
-    int digit_bits;
+    int digit_bits;  // GPU digit width per pass, 1..8 (0 only in workspace size queries)
     int cutoff;
     int log2S;
     int pack;  // 0 = by size, 1 = off, 2 = on (see Ctx::pack)
@@ -50,7 +50,10 @@ struct MemsetList {
 };
 
 int device_sms();
-bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, Tune *out);
+// K: the call's digit width (0 = not known: digit_bits stays 0 unless the
+// tune sets it, and workspace_bytes covers every width).
+bool resolve_tune(const pbit_tune *t, int64_t pool_size, int kb, int K, Tune *out);
+size_t workspace_bytes(int64_t ncap, int32_t L, int kb, Tune t, int sms);
 Sizes compute_sizes(int64_t ncap, int32_t L, int kb, const Tune &t, int sms);
 size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms);
 // small_lists: every list has at most kSmallList nodes (known on the host):
@@ -73,7 +76,7 @@ ListDesc pool_template(const pbit_pool *p);
 // Enqueue a sort of a pool with list ranges (d_offsets) or of one list
 // (d_offsets == nullptr: single_root, single_n); no synchronization.
 pbit_status enqueue_pool(const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
-                         const int64_t *d_offsets, int single_root, int64_t single_n, int M,
+                         const int64_t *d_offsets, int single_root, int64_t single_n, int M, int K,
                          int32_t *d_new_roots, const pbit_tune *tune, void *ws, size_t ws_bytes,
                          cudaStream_t s, Ctx *out, int stop_after = 0);
 

@@ -111,18 +111,20 @@ void tune_cache_store(int64_t pool_size, int32_t num_lists, int kb, const pbit_t
 // The candidates the autotuner times: the shared-memory cutoff and the
 // ruler stride of the list ranking.  (The pass digit width and tile are
 // compile-time constants of the pass kernel.)
+static const int kDigits[] = {4, 8};
 static const int kCutoffs[] = {128, 256, 512};
 static const int kStrides[] = {16, 32, 64, 128};
 
 static size_t candidate_ws_max(int64_t pool_size, int32_t num_lists, int kb) {
     size_t m = 0;
-    for (int c : kCutoffs)
-        for (int r : kStrides) {
-            pbit_tune t{0, c, r, 0};
-            size_t w = 0;
-            if (pbit_workspace_size(pool_size, num_lists, kb, &t, &w) == PBIT_OK)
-                m = std::max(m, w);
-        }
+    for (int d : kDigits)
+        for (int c : kCutoffs)
+            for (int r : kStrides) {
+                pbit_tune t{d, c, r, 0};
+                size_t w = 0;
+                if (pbit_workspace_size(pool_size, num_lists, kb, &t, &w) == PBIT_OK)
+                    m = std::max(m, w);
+            }
     size_t w = 0;
     if (pbit_workspace_size(pool_size, num_lists, kb, nullptr, &w) == PBIT_OK)
         m = std::max(m, w);
@@ -137,8 +139,8 @@ static bool check_batch_args(const pbit_pool *pool, int32_t num_lists, const int
 // Capture one sort call into g (batched when d_offsets != nullptr, else one
 // list given by root and n).
 static pbit_status capture(pbit_graph *g, const pbit_pool *pool, int32_t num_lists, const int32_t *d_roots,
-                           const int64_t *d_offsets, int32_t root, int64_t n, int32_t M, int32_t *d_new_roots,
-                           const pbit_tune *tune, void *ws, size_t ws_bytes) {
+                           const int64_t *d_offsets, int32_t root, int64_t n, int32_t M, int32_t K,
+                           int32_t *d_new_roots, const pbit_tune *tune, void *ws, size_t ws_bytes) {
     if (cudaGetDevice(&g->device) != cudaSuccess)
         return PBIT_ECUDA;
     cudaStream_t cs = nullptr;
@@ -150,8 +152,8 @@ static pbit_status capture(pbit_graph *g, const pbit_pool *pool, int32_t num_lis
     }
     const bool prof = prof_set(false);  // timing events are not part of a graph
     Ctx c;
-    pbit_status rc = enqueue_pool(pool, num_lists, d_roots, d_offsets, root, n, M, d_new_roots, tune, ws, ws_bytes,
-                                  cs, &c);
+    pbit_status rc = enqueue_pool(pool, num_lists, d_roots, d_offsets, root, n, M, K, d_new_roots, tune, ws,
+                                  ws_bytes, cs, &c);
     prof_set(prof);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &graph);  // always ends the capture
@@ -186,7 +188,7 @@ pbit_status pbit_graph_create_batched(const pbit_pool *pool, int32_t num_lists, 
     if (!out || !check_batch_args(pool, num_lists, d_roots, d_offsets, M, K, d_new_roots))
         return PBIT_EINVAL;
     pbit_graph *g = new pbit_graph();
-    pbit_status rc = capture(g, pool, num_lists, d_roots, d_offsets, 0, 0, M, d_new_roots, tune, ws, ws_bytes);
+    pbit_status rc = capture(g, pool, num_lists, d_roots, d_offsets, 0, 0, M, K, d_new_roots, tune, ws, ws_bytes);
     if (rc == PBIT_OK && cudaMallocHost((void **)&g->h_out, 64) != cudaSuccess)
         rc = PBIT_ECUDA;
     if (rc != PBIT_OK) {
@@ -205,7 +207,7 @@ pbit_status pbit_graph_create_single(const pbit_pool *pool, int32_t root, int64_
         return PBIT_EBADLIST;
     pbit_graph *g = new pbit_graph();
     g->single = true;
-    pbit_status rc = capture(g, pool, 1, nullptr, nullptr, root, n, M, nullptr, tune, ws, ws_bytes);
+    pbit_status rc = capture(g, pool, 1, nullptr, nullptr, root, n, M, K, nullptr, tune, ws, ws_bytes);
     if (rc == PBIT_OK && cudaMallocHost((void **)&g->h_out, 64) != cudaSuccess)
         rc = PBIT_ECUDA;
     if (rc != PBIT_OK) {
@@ -289,9 +291,11 @@ pbit_status pbit_autotune_batched(const pbit_pool *pool, int32_t num_lists, cons
     float best_t = INFINITY;
     pbit_tune best_c{};
     pbit_status last_err = PBIT_ENOMEM;
-    for (int ci = 0; rc == PBIT_OK && ci < (int)(sizeof kCutoffs / sizeof *kCutoffs); ++ci) {
-        for (int ri = 0; rc == PBIT_OK && ri < (int)(sizeof kStrides / sizeof *kStrides); ++ri) {
-            const pbit_tune cand{0, kCutoffs[ci], kStrides[ri], 0};
+    constexpr int nd = (int)(sizeof kDigits / sizeof *kDigits), nc = (int)(sizeof kCutoffs / sizeof *kCutoffs),
+                  nr = (int)(sizeof kStrides / sizeof *kStrides);
+    for (int ci = 0; rc == PBIT_OK && ci < nd * nc; ++ci) {
+        for (int ri = 0; rc == PBIT_OK && ri < nr; ++ri) {
+            const pbit_tune cand{kDigits[ci / nc], kCutoffs[ci % nc], kStrides[ri], 0};
             size_t need = 0;
             if (pbit_workspace_size(pool->pool_size, num_lists, pool->key_type, &cand, &need) != PBIT_OK ||
                 need > ws_bytes)
@@ -304,8 +308,8 @@ pbit_status pbit_autotune_batched(const pbit_pool *pool, int32_t num_lists, cons
                     rc = PBIT_ECUDA;
                     break;
                 }
-                st = enqueue_pool(pool, num_lists, d_roots, d_offsets, 0, 0, M, d_new_roots, &cand, ws, ws_bytes, s,
-                                  &c);
+                st = enqueue_pool(pool, num_lists, d_roots, d_offsets, 0, 0, M, K, d_new_roots, &cand, ws, ws_bytes,
+                                  s, &c);
                 int32_t dev_st = 0;
                 if (st == PBIT_OK &&
                     (cudaEventRecord(e1, s) != cudaSuccess ||
@@ -349,7 +353,6 @@ pbit_status pbit_autotune_batched(const pbit_pool *pool, int32_t num_lists, cons
         return rc;
     if (!std::isfinite(best_t))
         return last_err;
-    best_c.digit_bits = digit_bits();
     *best = best_c;
     if (best_ms)
         *best_ms = best_t;

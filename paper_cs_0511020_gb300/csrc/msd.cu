@@ -41,47 +41,11 @@ constexpr int kItems = 8;             // items per thread in a pass tile
 constexpr int kTileLog = 11;
 constexpr int kTile = kTPB * kItems;  // 2048 elements per pass tile
 static_assert(kTile == 1 << kTileLog, "tile is a power of two");
-constexpr int kD = 4;                 // GPU digit width (16 buckets, as the paper's K = 4)
+static_assert(kTile == kPassTile, "the plan kernels count tiles of kPassTile elements");
+constexpr int kD = 4;                 // widest window of these kernels (16 buckets, the paper's K = 4)
 constexpr int kBins = 1 << kD;
-constexpr int kScanRows = 256;        // tiles per scan chunk (one per thread)
+constexpr int kScanRows = kScanChunk; // tiles per scan chunk (one per thread)
 constexpr int kRowPad = kBins;        // extra next-pass rows per segment (one per bucket)
-
-__host__ __device__ constexpr int tiles_of(int64_t len, int64_t tile) { return (int)((len + tile - 1) / tile); }
-
-// ---------------------------------------------------------------- scans
-// Block-wide exclusive scan of one int per thread (blockDim.x <= 1024).
-__device__ int block_excl_scan(int v, int *total, int *sh /* >= 33 ints */) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o)
-            x += y;
-    }
-    if (lane == 31)
-        sh[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int s = (lane < nw) ? sh[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(kFull, s, o);
-            if (lane >= o)
-                s += y;
-        }
-        if (lane < nw)
-            sh[lane] = s;  // inclusive warp totals
-        if (lane == 31)
-            sh[32] = s;
-    }
-    __syncthreads();
-    int base = (wid > 0) ? sh[wid - 1] : 0;
-    *total = sh[32];
-    int r = base + x - v;
-    __syncthreads();
-    return r;
-}
 
 // Block-wide exclusive scan of 16-vectors (one per thread, 256 threads):
 // v[] becomes the exclusive prefix, tot[] the block totals (all threads).
@@ -159,11 +123,13 @@ __global__ void __launch_bounds__(1024) k_plan_init(Ctx c) {
             n = c.desc[i].n;
             start = c.desc[i].out_base;
         }
-        int is_fin = (i < L && n >= 1 && n <= c.cutoff) ? 1 : 0;
+        // (a stage check forces every list of two or more nodes into the passes)
+        const int cut = c.force_pass ? 1 : c.cutoff;
+        int is_fin = (i < L && n >= 1 && n <= cut) ? 1 : 0;
         // (a list's varying bits are not known yet: only M bits few enough
         // for the CTA finish qualify it directly; others go through seg_stats)
-        int is_mid = (i < L && n > c.cutoff && n <= kMidCap && c.M <= kMidSpan) ? 1 : 0;
-        int is_pend = (i < L && n > c.cutoff && !is_mid) ? 1 : 0;
+        int is_mid = (i < L && n > cut && n <= kMidCap && c.M <= kMidSpan && !c.force_pass) ? 1 : 0;
+        int is_pend = (i < L && n > cut && !is_mid) ? 1 : 0;
         int tiles = is_pend ? tiles_of(n, kTile) : 0;
         int tf, tp, tt, tm;
         int pf = block_excl_scan(is_fin, &tf, sh);
@@ -260,7 +226,7 @@ __global__ void __launch_bounds__(kTPB) k_seg_stats(Ctx c, int it) {
         const int64_t b0 = (int64_t)sg.start + (int64_t)k * kTile;
         const int cnt = (int)min((int64_t)kTile, (int64_t)sg.start + sg.len - b0);
         const KeyT *keys = reinterpret_cast<const KeyT *>(c.keyb[sg.buf & 1]);
-        const int hi = sg.hi, lo = max(hi - kD, 0);
+        const int hi = sg.hi, lo = max(hi - c.D, 0);
         const unsigned dmask = (1u << (hi - lo)) - 1u;
         my_elems += cnt;
         using U = typename KeyWord<KeyT>::U;  // 32-bit words for keys up to 4 bytes
@@ -351,12 +317,12 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
                 kind = sg.len <= c.cutoff ? 1 : 5;
             } else {
                 t = top_bit(v);
-                if (sg.len <= c.cutoff)
+                if (sg.len <= c.cutoff && !c.force_pass)
                     kind = 2;
                 else
-                    kind = (t >= sg.hi - kD) ? 3 : 4;
+                    kind = (t >= sg.hi - c.D) ? 3 : 4;
             }
-            if (kind >= 3 && mid_bucket(sg.len, v))
+            if (kind >= 3 && mid_bucket(sg.len, v) && !c.force_pass)
                 kind = 6;  // one CTA finishes it
         }
         const int tiles = kind == 4 ? tiles_of(sg.len, kTile) : 0;
@@ -382,7 +348,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
         } else if (kind == 3 || kind == 5) {
             const int64_t a = (int64_t)s_act_base + pa;
             if (a < c.seg_cap)
-                c.act[cur][a] = Seg{sg.start, sg.len, (int16_t)max(sg.hi - kD, 0), sg.hi, sg.buf,
+                c.act[cur][a] = Seg{sg.start, sg.len, (int16_t)max(sg.hi - c.D, 0), sg.hi, sg.buf,
                                     rbase + c.pend_tile_base[cur][s], kind == 5 ? 1 : 0};
             else
                 set_status(c.status, kStOverflow);
@@ -418,8 +384,10 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
     }
     __syncthreads();
     // tile, scan-chunk and next-row bases of all active segments of this pass
-    // (8 consecutive segments per thread per round)
+    // (8 consecutive segments per thread per round); the 8-bit passes count
+    // their tiles with a histogram kernel instead of next-pass rows
     constexpr int kPer = 8;
+    const bool wide = c.D > kD;
     const int A = (int)min((int64_t)s_act_base, c.seg_cap);
     long long my_elems = 0, my_final = 0;
     for (int r0 = 0; r0 < A; r0 += blockDim.x * kPer) {
@@ -430,7 +398,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
             const int nt = tiles_of(sa.len, kTile);
             tiles += nt;
             chunks += nt > 1 ? tiles_of(nt, kScanRows) : 0;
-            nrows += (sa.lo > 0 && !sa.final) ? nt + kRowPad : 0;
+            nrows += (!wide && sa.lo > 0 && !sa.final) ? nt + kRowPad : 0;
             my_elems += sa.len;
             if (sa.lo == 0 || sa.final)
                 my_final += sa.len;
@@ -447,7 +415,7 @@ __global__ void __launch_bounds__(1024) k_plan_pending(Ctx c, int it) {
             c.act_nrow_base[cur][a0 + u] = s_nrow_base + pn;
             pt += nt;
             pc += nt > 1 ? tiles_of(nt, kScanRows) : 0;
-            pn += (sa.lo > 0 && !sa.final) ? nt + kRowPad : 0;
+            pn += (!wide && sa.lo > 0 && !sa.final) ? nt + kRowPad : 0;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -817,7 +785,7 @@ __global__ void __launch_bounds__(kTPB, PassLayout<KeyT>::kMinBlocks) k_pass(Ctx
                 }
             }
         } else {
-            const int nlo = max(lo - kD, 0);
+            const int nlo = max(lo - c.D, 0);
             const unsigned nmask = (1u << (lo - nlo)) - 1u;
 #pragma unroll
             for (int u = 0; u < kItems; ++u) {
@@ -901,7 +869,7 @@ __device__ __forceinline__ int classify_bucket(const Ctx &c, int cur, int s, con
     *t_out = t;
     if ((int)cnt <= c.cutoff)
         return 2;
-    return (t + kD >= sg.lo) ? 3 : 4;
+    return (t + c.D >= sg.lo) ? 3 : 4;
 }
 
 // per active segment: how many next-active, pending, small/done buckets and
@@ -1030,7 +998,7 @@ __global__ void k_plan_write(Ctx c, int it) {
                 ++f;
             } else if (kd == 3 || kd == 5) {
                 if (a < c.seg_cap)
-                    c.act[nxt][a] = Seg{bstart, (int32_t)cnt, (int16_t)max(sg.lo - kD, 0), sg.lo,
+                    c.act[nxt][a] = Seg{bstart, (int32_t)cnt, (int16_t)max(sg.lo - c.D, 0), sg.lo,
                                         (sg.buf & 1) ^ 1, nrow, kd == 5 ? 1 : 0};
                 ++a;
             } else if (kd == 4) {
@@ -1069,12 +1037,25 @@ static void launch_iter_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     prof_mark("plan", s);
 }
 
+void launch_plan_pending(const Ctx &c, int it, cudaStream_t s) {
+    launch_pdl(k_plan_pending, dim3(1), dim3(1024), 0, s, c, it);
+    prof_mark("plan", s);
+}
+
+void launch_plan_scan(const Ctx &c, int it, cudaStream_t s) {
+    launch_pdl(k_plan_scan, dim3(1), dim3(1024), 0, s, c, it);
+}
+
 void launch_plan_init(const Ctx &c, cudaStream_t s) {
     launch_pdl(k_plan_init, dim3(1), dim3(1024), 0, s, c);
     prof_mark("plan", s);
 }
 
 void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms) {
+    if (c.D > kD) {  // windows of 5..8 bits: msd8.cu
+        launch_iteration8(c, it, s, sms);
+        return;
+    }
     switch (c.key_bytes) {
     case 1: launch_iter_t<uint8_t>(c, it, s, sms); break;
     case 2: launch_iter_t<uint16_t>(c, it, s, sms); break;
@@ -1087,6 +1068,7 @@ int64_t launches_per_iteration() { return 8; }
 int pass_tile() { return kTile; }
 int stat_tile() { return kTile; }
 int digit_bits() { return kD; }
+int max_digit_bits() { return wide_digit_bits(); }
 int scan_rows() { return kScanRows; }
 int row_pad() { return kRowPad; }
 

@@ -1,0 +1,601 @@
+// msd8.cu -- MSD digit passes with windows of up to 8 bits (256 buckets).
+//
+// The paper measures Pbit with K = 4, 8 and 16 bits per level (Sec. "The
+// length of bit pattern"): a wider digit means fewer levels over the list.
+// These kernels run one level per pass with a window of 5..8 bits (K = 16 is
+// two passes of 8 bits per level).  They keep the structure of the 4-bit
+// passes (msd.cu) -- the lists still to be split are segments of the order
+// buffers, one pass splits all of them stably into buckets laid out in
+// ascending digit order, small and mid-size buckets go to the finishes -- but
+// count differently: with 256 buckets a table of next-pass counts per output
+// tile no longer fits in shared memory, so every pass is preceded by a
+// histogram kernel that counts each tile's digits (one extra read of the keys,
+// w bytes per element, against the 2 (w + 4) bytes the pass moves).
+//
+// One iteration (= one level for every live segment):
+//   hist8         pending segments: per-tile 256-bin counts of the window
+//                 below their top bit, and the AND/OR of their keys
+//   plan_pending  (shared with the 4-bit passes) pending -> active / small /
+//                 mid / done / pending again at the top varying bit; tile and
+//                 scan-chunk bases of the active segments
+//   tile_scan8    per chunk of 256 tiles: exclusive prefixes of the counts
+//   chunk_scan8   per segment: prefixes over its chunks, then the start of
+//                 each of its 256 buckets
+//   pass8         per tile: warp-ballot ranking with per-warp counters in
+//                 shared memory, stable scatter through shared memory,
+//                 coalesced write-out per digit run
+//   plan_count8 / plan_scan / plan_write8
+//                 output buckets -> small (warp finish) / mid-size (CTA
+//                 finish) / pending for the next iteration
+#include "pbit_internal.cuh"
+
+namespace pbit {
+
+constexpr int k8TPB = 256;
+constexpr int k8Warps = k8TPB / 32;
+constexpr int k8Items = 8;
+constexpr int k8Tile = k8TPB * k8Items;
+static_assert(k8Tile == kPassTile, "the plan kernels count tiles of kPassTile elements");
+constexpr int k8Bits = 8;
+constexpr int k8Bins = 1 << k8Bits;
+static_assert(k8Bins == k8TPB, "one thread per bucket in the per-tile steps");
+
+// ------------------------------------------------------------------ hist8
+// For every tile of every pending segment: the counts of the 256 digits of
+// the window [max(hi - D, 0), hi) (row g of tcnt: plain stores), and the
+// AND/OR of the segment's keys (merged per CTA per segment).
+template <typename KeyT>
+__global__ void __launch_bounds__(k8TPB) k_hist8(Ctx c, int it) {
+    griddep_wait();
+    __shared__ uint32_t s_h[k8Warps][k8Bins];
+    __shared__ unsigned long long s_and, s_or;
+    __shared__ int s_aseg;
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1;
+    const int P = c.ctr->pend_count[cur];
+    const int ntiles = c.ctr->stat_tiles[cur];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    long long my_elems = 0;
+    for (int w = 0; w < k8Warps; ++w)
+        s_h[w][tid] = 0;
+    if (tid == 0) {
+        s_and = ~0ull;
+        s_or = 0ull;
+        s_aseg = -1;
+    }
+    using U = typename KeyWord<KeyT>::U;
+    for (int g = blockIdx.x; g < ntiles; g += gridDim.x) {
+        __syncthreads();  // the previous tile's counts are stored and cleared
+        const int s = upper_index(c.pend_tile_base[cur], P, g);
+        if (tid == 0 && s != s_aseg) {  // AND/OR are merged per segment, not per tile
+            if (s_aseg >= 0) {
+                atomicAnd(&c.pand[cur][s_aseg], s_and);
+                atomicOr(&c.por[cur][s_aseg], s_or);
+            }
+            s_and = ~0ull;
+            s_or = 0ull;
+            s_aseg = s;
+        }
+        __syncthreads();  // the reset precedes this tile's merges
+        const Seg sg = c.pend[cur][s];
+        const int k = g - c.pend_tile_base[cur][s];
+        const int64_t b0 = (int64_t)sg.start + (int64_t)k * k8Tile;
+        const int cnt = (int)min((int64_t)k8Tile, (int64_t)sg.start + sg.len - b0);
+        const KeyT *keys = reinterpret_cast<const KeyT *>(c.keyb[sg.buf & 1]) + b0;
+        const int hi = sg.hi, lo = max(hi - c.D, 0);
+        const unsigned dmask = (1u << (hi - lo)) - 1u;
+        my_elems += cnt;
+        U kv[k8Items];
+#pragma unroll
+        for (int u = 0; u < k8Items; ++u) {
+            const int pos = u * k8TPB + tid;
+            kv[u] = pos < cnt ? (U)keys[pos] : (U)0;
+        }
+        U w_and = ~(U)0, w_or = 0;
+#pragma unroll
+        for (int u = 0; u < k8Items; ++u) {
+            if (u * k8TPB + tid < cnt) {
+                w_and &= kv[u];
+                w_or |= kv[u];
+                atomicAdd(&s_h[wid][(unsigned)(kv[u] >> lo) & dmask], 1u);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            w_and &= __shfl_xor_sync(kFull, w_and, o);
+            w_or |= __shfl_xor_sync(kFull, w_or, o);
+        }
+        if (lane == 0) {  // keys are zero-extended to 64 bits
+            atomicAnd(&s_and, (unsigned long long)w_and);
+            atomicOr(&s_or, (unsigned long long)w_or);
+        }
+        __syncthreads();
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < k8Warps; ++w) {
+            sum += s_h[w][tid];
+            s_h[w][tid] = 0;
+        }
+        if ((int64_t)g < c.row_cap)
+            c.tcnt[cur][(int64_t)g * k8Bins + tid] = sum;
+        else
+            set_status(c.status, kStOverflow);
+    }
+    if (tid == 0) {
+        if (s_aseg >= 0) {
+            atomicAnd(&c.pand[cur][s_aseg], s_and);
+            atomicOr(&c.por[cur][s_aseg], s_or);
+        }
+        if (my_elems)
+            atomicAdd((unsigned long long *)&c.ctr->stat_elems[it], (unsigned long long)my_elems);
+    }
+}
+
+// ------------------------------------------------------------- tile_scan8
+// Per chunk of kScanChunk tiles of an active segment, one thread per digit:
+// each tile's counts become the exclusive prefix within the chunk, and the
+// chunk totals go to ctot.
+__global__ void __launch_bounds__(k8TPB) k_tile_scan8(Ctx c, int it) {
+    griddep_wait();
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1;
+    const int A = c.ctr->act_count[cur];
+    const int nch = c.ctr->num_chunks[cur];
+    const int d = threadIdx.x;
+    for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int a = upper_index(c.act_chunk_base[cur], A, ch);
+        const Seg sg = c.act[cur][a];
+        const int lc = ch - c.act_chunk_base[cur][a];
+        const int nt = c.act_tile_base[cur][a + 1] - c.act_tile_base[cur][a];
+        const int t0 = lc * kScanChunk, t1 = min(nt, t0 + kScanChunk);
+        uint32_t *col = c.tcnt[cur] + ((int64_t)sg.row + t0) * k8Bins + d;
+        uint32_t run = 0;
+        int t = 0;
+        for (; t + 8 <= t1 - t0; t += 8) {  // eight loads in flight, then the running sum
+            uint32_t x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                x[u] = col[(int64_t)(t + u) * k8Bins];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                col[(int64_t)(t + u) * k8Bins] = run;
+                run += x[u];
+            }
+        }
+        for (; t < t1 - t0; ++t) {
+            const uint32_t x = col[(int64_t)t * k8Bins];
+            col[(int64_t)t * k8Bins] = run;
+            run += x;
+        }
+        c.ctot[(int64_t)ch * k8Bins + d] = run;
+    }
+}
+
+// ------------------------------------------------------------ chunk_scan8
+// One CTA per active segment, one thread per digit: exclusive prefixes over
+// the segment's chunks (in place), then the start of each bucket within the
+// segment (exclusive prefix over the digits of its histogram) in act_hist.
+__global__ void __launch_bounds__(k8TPB) k_chunk_scan8(Ctx c, int it) {
+    griddep_wait();
+    __shared__ int sh[40];
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1;
+    const int A = c.ctr->act_count[cur];
+    const int d = threadIdx.x;
+    for (int a = blockIdx.x; a < A; a += gridDim.x) {
+        const int nt = c.act_tile_base[cur][a + 1] - c.act_tile_base[cur][a];
+        uint32_t h = 0;
+        if (nt == 1) {
+            h = c.tcnt[cur][(int64_t)c.act[cur][a].row * k8Bins + d];
+        } else {
+            const int c0 = c.act_chunk_base[cur][a], c1 = c.act_chunk_base[cur][a + 1];
+            for (int ch = c0; ch < c1; ++ch) {
+                uint32_t *p = c.ctot + (int64_t)ch * k8Bins + d;
+                const uint32_t t = *p;
+                *p = h;
+                h += t;
+            }
+        }
+        int tot;
+        const int ex = block_excl_scan((int)h, &tot, sh);
+        c.act_hist[cur][(int64_t)a * k8Bins + d] = (uint32_t)ex;
+    }
+}
+
+// ------------------------------------------------------------------ pass8
+struct Pass8Smem {
+    uint32_t wcnt[k8Warps][k8Bins];  // per-warp digit counts -> each warp's first tile slot per digit
+    int32_t gdelta[k8Bins];          // output position - tile slot, per digit
+    int sh[40];                      // block scan scratch
+    int32_t st_seg[2], st_cnt[2], st_k[2], st_shk[2], st_shi[2];
+    int32_t nt[2];
+    alignas(8) uint64_t bar[2];
+};
+
+template <typename KeyT>
+struct Pass8Layout {
+    static constexpr int kKeyBytes = k8Tile * (int)sizeof(KeyT) + 32;
+    static constexpr int kIdxBytes = k8Tile * 4 + 32;
+    static constexpr int kStage = ((kKeyBytes + kIdxBytes + 127) / 128) * 128;
+    static constexpr int kHdr = ((int)sizeof(Pass8Smem) + 127) / 128 * 128;
+    static constexpr int kTotal = kHdr + 2 * kStage;
+    static constexpr int kMinBlocks = sizeof(KeyT) == 8 ? 3 : 4;
+};
+
+// Issue the bulk copies of tile g into stage st (one thread).
+template <typename KeyT>
+__device__ __forceinline__ void pass8_issue(const Ctx &c, int cur, int g, int st, Pass8Smem &S,
+                                            unsigned char *stage, int A) {
+    const int s = upper_index(c.act_tile_base[cur], A, g);
+    const Seg sg = c.act[cur][s];
+    const int k = g - c.act_tile_base[cur][s];
+    const int64_t start = (int64_t)sg.start + (int64_t)k * k8Tile;
+    const int cnt = (int)min((int64_t)k8Tile, (int64_t)sg.start + sg.len - start);
+    constexpr int W = (int)sizeof(KeyT);
+    const unsigned char *kb = c.keyb[sg.buf & 1];
+    const unsigned char *ib = reinterpret_cast<const unsigned char *>(c.idxb[sg.buf & 1]);
+    // 16-byte aligned copies covering [start, start + cnt); the order buffers
+    // carry 64 bytes of slack behind their end for the rounding up
+    const int64_t k_lo = (start * W) & ~15ll, k_hi = ((start + cnt) * W + 15) & ~15ll;
+    const int64_t i_lo = (start * 4) & ~15ll, i_hi = ((start + cnt) * 4 + 15) & ~15ll;
+    S.st_seg[st] = s;
+    S.st_cnt[st] = cnt;
+    S.st_k[st] = k;
+    S.st_shk[st] = (int32_t)((start * W - k_lo) / W);
+    S.st_shi[st] = (int32_t)((start * 4 - i_lo) / 4);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&S.bar[st], (uint32_t)((k_hi - k_lo) + (i_hi - i_lo)));
+    bulk_g2s(stage, kb + k_lo, (uint32_t)(k_hi - k_lo), &S.bar[st]);
+    bulk_g2s(stage + Pass8Layout<KeyT>::kKeyBytes, ib + i_lo, (uint32_t)(i_hi - i_lo), &S.bar[st]);
+}
+
+// Persistent CTAs take tiles from a counter; the bulk copy of the next tile
+// is in flight while the current one is ranked and written.  Ranking: for
+// each 32-element group a warp finds, with one ballot per digit bit, the
+// lanes holding the same digit (peers); the lowest of them adds the group's
+// count to the warp's shared counter of that digit and passes the old value
+// to its peers, so every element learns how many elements with its digit
+// came before it in the warp's part of the tile (memory order = warp, group,
+// lane: the order is stable).
+template <typename KeyT>
+__global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(Ctx c, int it) {
+    griddep_wait();
+    extern __shared__ __align__(128) unsigned char smem[];
+    Pass8Smem &S = *reinterpret_cast<Pass8Smem *>(smem);
+    unsigned char *stages = smem + Pass8Layout<KeyT>::kHdr;
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned lt = lanemask_lt();
+    const int A = c.ctr->act_count[cur];
+    const int ntiles = c.ctr->num_tiles[cur];
+    if (A == 0 || ntiles == 0)
+        return;
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
+    }
+#pragma unroll
+    for (int w = 0; w < k8Warps; ++w)
+        S.wcnt[w][tid] = 0;
+    uint32_t phases = 0;  // bit b: parity of stage b's barrier
+    int st = 0;
+    if (tid == 0) {
+        const int g = atomicAdd(&c.ctr->tile_ctr[it], 1);
+        S.nt[0] = g;
+        if (g < ntiles)
+            pass8_issue<KeyT>(c, cur, g, 0, S, stages, A);
+    }
+    __syncthreads();
+    int g = S.nt[0];
+    while (g < ntiles) {
+        unsigned char *stage = stages + st * Pass8Layout<KeyT>::kStage;
+        if (tid == 0) {  // prefetch the next tile into the other stage
+            const int g2 = atomicAdd(&c.ctr->tile_ctr[it], 1);
+            S.nt[st ^ 1] = g2;
+            if (g2 < ntiles)
+                pass8_issue<KeyT>(c, cur, g2, st ^ 1, S, stages + (st ^ 1) * Pass8Layout<KeyT>::kStage, A);
+        }
+        const int s = S.st_seg[st];
+        const int k = S.st_k[st];
+        const int cnt = S.st_cnt[st];
+        const Seg sg = c.act[cur][s];
+        const int lo = sg.lo, width = sg.hi - sg.lo;
+        const unsigned dmask = (1u << width) - 1u;
+        // output position of this tile's first element of digit tid: bucket
+        // start + the digit's count in the segment's earlier tiles (loads in
+        // flight while the copy lands)
+        int32_t gb = sg.start + (int32_t)c.act_hist[cur][(int64_t)s * k8Bins + tid];
+        if (k > 0) {
+            const int ch = c.act_chunk_base[cur][s] + k / kScanChunk;
+            gb += (int32_t)(c.ctot[(int64_t)ch * k8Bins + tid] + c.tcnt[cur][((int64_t)sg.row + k) * k8Bins + tid]);
+        }
+        // one thread waits for the copy (acquire), the barrier publishes it
+        const bool landed = (tid != 0) || mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
+        if (!__syncthreads_and(landed)) {
+            set_status(c.status, PBIT_ETIMEOUT);
+            if (tid == 0) {  // wait (bounded) for the copies still in flight before leaving
+                mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
+                if (S.nt[st ^ 1] < ntiles)
+                    mbar_wait_bounded(&S.bar[st ^ 1], (phases >> (st ^ 1)) & 1u, 1ll << 26);
+            }
+            return;
+        }
+        phases ^= 1u << st;
+        const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + S.st_shk[st];
+        const int32_t *si = reinterpret_cast<const int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes) + S.st_shi[st];
+
+        // ---- ranking within the warp
+        KeyT key[k8Items];
+        int32_t idx[k8Items];
+        uint32_t rnk[k8Items];
+        uint32_t *wc = S.wcnt[wid];
+#pragma unroll
+        for (int i = 0; i < k8Items; ++i) {
+            const int pos = wid * (32 * k8Items) + i * 32 + lane;
+            const bool valid = pos < cnt;
+            key[i] = valid ? sk[pos] : (KeyT)0;
+            idx[i] = valid ? si[pos] : 0;
+            const unsigned dig = digit_of<KeyT>(key[i], lo, dmask);
+            unsigned peers = __ballot_sync(kFull, valid);
+#pragma unroll
+            for (int b = 0; b < k8Bits; ++b) {
+                if (b < width) {  // warp-uniform
+                    const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
+                    peers &= ((dig >> b) & 1u) ? bb : ~bb;
+                }
+            }
+            const int leader = __ffs(peers) - 1;  // (an invalid lane's value is never used)
+            uint32_t before = 0;
+            if (valid && lane == leader)
+                before = atomicAdd(&wc[dig], (uint32_t)__popc(peers));
+            rnk[i] = __shfl_sync(kFull, before, leader & 31) + (uint32_t)__popc(peers & lt);
+        }
+        __syncthreads();
+        // ---- tile offsets per digit (thread tid = digit), each warp's first slot
+        {
+            uint32_t cw[k8Warps];
+            uint32_t tot = 0;
+#pragma unroll
+            for (int w = 0; w < k8Warps; ++w) {
+                cw[w] = S.wcnt[w][tid];
+                tot += cw[w];
+            }
+            int ttot;
+            uint32_t run = (uint32_t)block_excl_scan((int)tot, &ttot, S.sh);
+            S.gdelta[tid] = gb - (int32_t)run;
+#pragma unroll
+            for (int w = 0; w < k8Warps; ++w) {
+                S.wcnt[w][tid] = run;
+                run += cw[w];
+            }
+        }
+        __syncthreads();
+        // ---- local scatter into the stage buffer (all items are in registers)
+        KeyT *ok = reinterpret_cast<KeyT *>(stage);
+        int32_t *oi = reinterpret_cast<int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes);
+#pragma unroll
+        for (int i = 0; i < k8Items; ++i) {
+            const int pos = wid * (32 * k8Items) + i * 32 + lane;
+            if (pos < cnt) {
+                const uint32_t lp = wc[digit_of<KeyT>(key[i], lo, dmask)] + rnk[i];
+                ok[lp] = key[i];
+                oi[lp] = idx[i];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < k8Warps; ++w)  // counters of the next tile
+            S.wcnt[w][tid] = 0;
+        // ---- coalesced write-out: slot j goes to gdelta[its digit] + j
+        if (lo == 0 || sg.final) {
+#pragma unroll
+            for (int u = 0; u < k8Items; ++u) {
+                const int j = u * k8TPB + tid;
+                if (j < cnt) {
+                    const int dst = S.gdelta[digit_of<KeyT>(ok[j], lo, dmask)] + j;
+                    if ((unsigned)(dst - sg.start) >= (unsigned)sg.len)
+                        set_status(c.status, kStOverflow);
+                    else
+                        c.F[dst] = oi[j];
+                }
+            }
+        } else {
+            KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(sg.buf & 1) ^ 1]);
+            int32_t *oidx = c.idxb[(sg.buf & 1) ^ 1];
+#pragma unroll
+            for (int u = 0; u < k8Items; ++u) {
+                const int j = u * k8TPB + tid;
+                if (j < cnt) {
+                    const KeyT kk = ok[j];
+                    const int dst = S.gdelta[digit_of<KeyT>(kk, lo, dmask)] + j;
+                    if ((unsigned)(dst - sg.start) >= (unsigned)sg.len) {
+                        set_status(c.status, kStOverflow);
+                    } else {
+                        okey[dst] = kk;
+                        oidx[dst] = oi[j];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        g = S.nt[st ^ 1];
+        st ^= 1;
+    }
+}
+
+// ------------------------------------------------------------------ plan8
+// Where an output bucket of an 8-bit pass goes (its varying bits are not
+// known: they are counted by the next histogram if it stays in the passes):
+// 0 none, 1 one node (copied), 2 small (warp finish on its low `lo` bits),
+// 4 pending for the next iteration, 6 mid-size (CTA finish; a bucket with at
+// most kMidSpan bits left always qualifies).
+__device__ __forceinline__ int classify8(const Ctx &c, uint32_t cnt, int lo) {
+    if (cnt == 0)
+        return 0;
+    if (cnt == 1)
+        return 1;
+    if ((int)cnt <= c.cutoff)
+        return 2;
+    if ((int)cnt <= kMidCap && lo <= kMidSpan)
+        return 6;
+    return 4;
+}
+
+// Lane l of the warp of a segment looks at digits 8l .. 8l + 7.
+__device__ __forceinline__ uint32_t bucket_len8(const Ctx &c, int cur, int64_t a, int d, int len) {
+    const uint32_t *bs = c.act_hist[cur] + a * k8Bins;
+    const uint32_t s0 = bs[d];
+    const uint32_t s1 = d + 1 < k8Bins ? bs[d + 1] : (uint32_t)len;
+    return s1 - s0;
+}
+
+// One warp per active segment: how many pending, small and mid-size buckets
+// (and stats tiles) its 256 buckets produce.
+__global__ void k_plan_count8(Ctx c, int it) {
+    griddep_wait();
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1;
+    const int A = c.ctr->act_count[cur];
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < A; a += nw) {
+        const Seg sg = c.act[cur][a];
+        int np = 0, nf = 0, nt = 0, nm = 0;
+        if (sg.lo > 0 && !sg.final) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t cnt = bucket_len8(c, cur, a, lane * 8 + j, sg.len);
+                const int kd = classify8(c, cnt, sg.lo);
+                np += kd == 4;
+                nf += kd == 1 || kd == 2;
+                nt += kd == 4 ? tiles_of(cnt, kPassTile) : 0;
+                nm += kd == 6;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            np += __shfl_xor_sync(kFull, np, o);
+            nf += __shfl_xor_sync(kFull, nf, o);
+            nt += __shfl_xor_sync(kFull, nt, o);
+            nm += __shfl_xor_sync(kFull, nm, o);
+        }
+        if (lane == 0) {
+            c.plan_cnt[a] = make_int4(0, np, nf, nt);
+            c.plan_mid[a] = nm;
+        }
+    }
+}
+
+__device__ __forceinline__ int warp_excl_sum(int v, int lane) {
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    return x - v;
+}
+
+// One warp per active segment: write its buckets' records at the offsets
+// plan_scan computed, in ascending digit order.
+__global__ void k_plan_write8(Ctx c, int it) {
+    griddep_wait();
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int cur = it & 1, nxt = cur ^ 1;
+    const int A = c.ctr->act_count[cur];
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t a = gw; a < A; a += nw) {
+        const Seg sg = c.act[cur][a];
+        if (sg.lo == 0 || sg.final)
+            continue;  // the pass wrote it to its final place
+        uint32_t cnt[8];
+        int np = 0, nf = 0, nt = 0, nm = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            cnt[j] = bucket_len8(c, cur, a, lane * 8 + j, sg.len);
+            const int kd = classify8(c, cnt[j], sg.lo);
+            np += kd == 4;
+            nf += kd == 1 || kd == 2;
+            nt += kd == 4 ? tiles_of(cnt[j], kPassTile) : 0;
+            nm += kd == 6;
+        }
+        const int4 o = c.plan_cnt[a];
+        int64_t p = o.y + warp_excl_sum(np, lane);
+        int64_t f = o.z + warp_excl_sum(nf, lane);
+        int64_t tb = o.w + warp_excl_sum(nt, lane);
+        int64_t m = c.plan_mid[a] + warp_excl_sum(nm, lane);
+        const int nbuf = (sg.buf & 1) ^ 1;
+        int32_t bstart = sg.start + (int32_t)c.act_hist[cur][a * k8Bins + lane * 8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int kd = classify8(c, cnt[j], sg.lo);
+            if (kd == 6) {
+                if (m < c.mid_cap)
+                    c.mid[m] = Fin{bstart, (int32_t)cnt[j], sg.lo, (1 << 8) | nbuf};
+                ++m;
+            } else if (kd == 1 || kd == 2) {
+                if (f < c.fin_cap)
+                    c.fin[f] = Fin{bstart, (int32_t)cnt[j], kd == 2 ? sg.lo : 0, ((kd == 2 ? 1 : 0) << 8) | nbuf};
+                ++f;
+            } else if (kd == 4) {
+                if (p < c.seg_cap) {
+                    c.pend[nxt][p] = Seg{bstart, (int32_t)cnt[j], 0, sg.lo, nbuf, 0, 0};
+                    c.pend_tile_base[nxt][p] = (int32_t)tb;
+                }
+                tb += tiles_of(cnt[j], kPassTile);
+                ++p;
+            }
+            bstart += (int32_t)cnt[j];
+        }
+    }
+}
+
+// ------------------------------------------------------------- launchers
+void launch_plan_pending(const Ctx &c, int it, cudaStream_t s);  // msd.cu
+void launch_plan_scan(const Ctx &c, int it, cudaStream_t s);     // msd.cu
+
+template <typename KeyT>
+static void launch_iter8_t(const Ctx &c, int it, cudaStream_t s, int sms) {
+    const int smem = Pass8Layout<KeyT>::kTotal;
+    cudaFuncSetAttribute(k_pass8<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    const int per_sm = Pass8Layout<KeyT>::kMinBlocks;
+    const unsigned wblocks = (unsigned)max(1, min(sms * 8, (int)((c.seg_cap + 7) / 8)));  // 8 warps per CTA
+    const unsigned sblocks = (unsigned)max(1, min(sms * 8, (int)c.seg_cap));
+    launch_pdl(k_hist8<KeyT>, dim3(sms * 8), dim3(k8TPB), 0, s, c, it);
+    prof_mark("seg_stats", s);
+    launch_plan_pending(c, it, s);
+    launch_pdl(k_tile_scan8, dim3(sms * 4), dim3(k8TPB), 0, s, c, it);
+    launch_pdl(k_chunk_scan8, dim3(sblocks), dim3(k8TPB), 0, s, c, it);
+    prof_mark("scan", s);
+    launch_pdl(k_pass8<KeyT>, dim3(sms * per_sm), dim3(k8TPB), smem, s, c, it);
+    prof_mark("pass", s);
+    launch_pdl(k_plan_count8, dim3(wblocks), dim3(256), 0, s, c, it);
+    launch_plan_scan(c, it, s);
+    launch_pdl(k_plan_write8, dim3(wblocks), dim3(256), 0, s, c, it);
+    prof_mark("plan", s);
+}
+
+void launch_iteration8(const Ctx &c, int it, cudaStream_t s, int sms) {
+    switch (c.key_bytes) {
+    case 1: launch_iter8_t<uint8_t>(c, it, s, sms); break;
+    case 2: launch_iter8_t<uint16_t>(c, it, s, sms); break;
+    case 4: launch_iter8_t<uint32_t>(c, it, s, sms); break;
+    default: launch_iter8_t<unsigned long long>(c, it, s, sms); break;
+    }
+}
+
+int wide_digit_bits() { return k8Bits; }
+
+}  // namespace pbit

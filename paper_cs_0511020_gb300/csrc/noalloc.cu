@@ -78,7 +78,7 @@ extern "C" pbit_status pbit_sort_list_noalloc(const pbit_pool *pool, int32_t roo
         return rc;
     Tune t;
     const pbit_tune sparse{0, 0, 32, 0};  // sparse rulers: fewer walk warps, less chunk slack to fit the array
-    if (!resolve_tune(&sparse, n, pool->key_type, &t))
+    if (!resolve_tune(&sparse, n, pool->key_type, K, &t))
         return PBIT_EINVAL;
     const Sizes z = compute_sizes(n, 1, pool->key_type, t, sms);
     if (bind(z, nullptr, nullptr, nullptr) > kScratchBytes)

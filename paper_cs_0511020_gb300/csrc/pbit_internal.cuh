@@ -64,6 +64,11 @@ constexpr int kMidSpan = 16;
 // Lists of at most kSmallList nodes are sorted by one kernel, one CTA each.
 constexpr int kSmallList = 4096;  // ... when at most this many of their key bits vary (4 windows)
 
+// Elements per MSD pass tile (4- and 8-bit passes alike) and tiles per scan
+// chunk: the plan kernels count tiles and chunks in these units.
+constexpr int kPassTile = 2048;
+constexpr int kScanChunk = 256;
+
 // Work counters that many CTAs hit at once sit on their own 128-byte lines
 // (an atomic on a line is serialized in one L2 slice).
 struct alignas(128) HotCounter {
@@ -101,12 +106,13 @@ struct Ctx {
     int32_t num_lists;
     int32_t key_bytes;
     int32_t M;
-    int32_t D;          // GPU digit width per pass (4)
+    int32_t D;          // GPU digit width per pass (1..8; above 4: the 256-bucket passes)
     int32_t log2S;      // ruler stride S = 1 << log2S
     int32_t cutoff;     // buckets <= cutoff are finished in shared memory
     int32_t flags;      // PBIT_SIGNED | PBIT_DESCENDING | PBIT_FLOAT | PBIT_DOUBLY
     int32_t CH;         // ranking chunk entries
     int32_t shared_pool;       // all lists in one pool (blocked relink possible)
+    int32_t force_pass;        // stage check: lists skip the finishes and take a global pass
     int64_t desc_next_stride;  // next[] stride of that pool
     int64_t ncap;       // capacity of the order buffers (pool size)
     int32_t R0;         // hash-ruler tasks
@@ -141,12 +147,13 @@ struct Ctx {
     // keyb[1] / idxb[1] / F, which are idle until the first pass.
     unsigned char *pack;
     Seg *act[2];
-    uint32_t *act_hist[2];      // seg_cap x 16 : histogram of the pass window
+    uint32_t *act_hist[2];      // seg_cap x 16 : histogram of the pass window (D > 4: seg_cap x 256
+                                // bucket starts within the segment)
     int32_t *act_tile_base[2];  // seg_cap + 1
     int32_t *act_chunk_base[2]; // seg_cap + 1 : first scan chunk of the segment
     int32_t *act_nrow_base[2];  // seg_cap + 1 : first tcnt row of its buckets in the next pass
-    uint32_t *tcnt[2];          // row_cap x 16 : digit counts per pass tile -> exclusive prefixes
-    uint32_t *ctot;             // scan_cap x 16 : per scan chunk totals -> exclusive prefixes
+    uint32_t *tcnt[2];          // row_cap x 16 (D > 4: 256) : digit counts per pass tile -> exclusive prefixes
+    uint32_t *ctot;             // scan_cap x 16 (D > 4: 256) : per scan chunk totals -> exclusive prefixes
     int64_t row_cap;
     int64_t scan_cap;
     unsigned long long *band[2];// seg_cap x 16
@@ -208,6 +215,45 @@ __device__ __forceinline__ int32_t upper_index(const int32_t *a, int32_t n, int3
     }
     return lo;
 }
+
+// ----------------------------------------------------------------- scans
+__host__ __device__ constexpr int tiles_of(int64_t len, int64_t tile) { return (int)((len + tile - 1) / tile); }
+
+// ---------------------------------------------------------------- scans
+// Block-wide exclusive scan of one int per thread (blockDim.x <= 1024).
+__device__ __forceinline__ int block_excl_scan(int v, int *total, int *sh /* >= 33 ints */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int s = (lane < nw) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, s, o);
+            if (lane >= o)
+                s += y;
+        }
+        if (lane < nw)
+            sh[lane] = s;  // inclusive warp totals
+        if (lane == 31)
+            sh[32] = s;
+    }
+    __syncthreads();
+    int base = (wid > 0) ? sh[wid - 1] : 0;
+    *total = sh[32];
+    int r = base + x - v;
+    __syncthreads();
+    return r;
+}
+
 
 // Keys up to 32 bits are handled in 32-bit words (digit shifts, AND/OR).
 template <typename KeyT>
@@ -365,7 +411,8 @@ void launch_relink_direct(const Ctx &c, cudaStream_t s, int sms);
 void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds);
 void launch_validate_emit(const Ctx &c, cudaStream_t s, int sms);
 void launch_plan_init(const Ctx &c, cudaStream_t s);
-void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms);
+void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms);   // D <= 4 here, else:
+void launch_iteration8(const Ctx &c, int it, cudaStream_t s, int sms);  // windows of 5..8 bits (msd8.cu)
 void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms);
 void launch_check_done(const Ctx &c, int iters, cudaStream_t s);
 int64_t launches_per_iteration();
@@ -375,7 +422,9 @@ int relink_bucket_bits(const Ctx &c);
 int relink_max_buckets();
 int pass_tile();
 int stat_tile();
-int digit_bits();
+int digit_bits();       // widest window of the 16-bucket passes (4)
+int wide_digit_bits();  // widest window of the 256-bucket passes (8)
+int max_digit_bits();
 int scan_rows();
 int row_pad();
 

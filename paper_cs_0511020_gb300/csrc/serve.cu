@@ -51,8 +51,8 @@ struct SrvSlot {
 };
 
 static bool compatible(const SrvReq *a, const SrvReq *b) {
-    return a->pool.key_type == b->pool.key_type && a->pool.flags == b->pool.flags && a->M == b->M && !a->solo &&
-           !b->solo;
+    return a->pool.key_type == b->pool.key_type && a->pool.flags == b->pool.flags && a->M == b->M && a->K == b->K &&
+           !a->solo && !b->solo;
 }
 
 static size_t batch_ws(int64_t nodes, int32_t lists, int kb) {
@@ -125,7 +125,7 @@ static pbit_status launch_batch(SrvSlot &slot, const std::vector<SrvReq *> &b, i
         slot.h_desc[i] = d;
     }
     Tune t;
-    resolve_tune(nullptr, nodes, r0->pool.key_type, &t);
+    resolve_tune(nullptr, nodes, r0->pool.key_type, r0->K, &t);
     const int sms = device_sms();
     Sizes z = compute_sizes(nodes, L, r0->pool.key_type, t, sms);
     Ctx c;

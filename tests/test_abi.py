@@ -69,7 +69,8 @@ def test_tune_validation(so):
     f.restype = ctypes.c_int
     f.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
     out = ctypes.c_size_t(0)
-    for tune, ok in (((4, 0, 0, 0), True), ((8, 0, 0, 0), False), ((0, 512, 0, 0), True), ((0, 513, 0, 0), False),
+    for tune, ok in (((4, 0, 0, 0), True), ((8, 0, 0, 0), True), ((1, 0, 0, 0), True), ((9, 0, 0, 0), False),
+                     ((0, 512, 0, 0), True), ((0, 513, 0, 0), False),
                      ((0, 0, 64, 0), True), ((0, 0, 48, 0), False), ((0, 0, 1 << 13, 0), False),
                      ((0, 0, 0, 2), True), ((0, 0, 0, 3), False), ((0, 0, 0, -1), False)):
         t = pbit.Tune(*tune)
@@ -99,10 +100,21 @@ def test_autotune_workspace_covers_every_candidate(so):
     from paper_cs_0511020_gb300 import pbit
     n, L = 1 << 22, 64
     big = pbit.autotune_workspace_size(n, L, 4)
-    for c in (128, 256, 512):
-        for r in (16, 32, 64, 128):
-            assert big >= pbit.workspace_size(n, L, 4, {"smem_cutoff": c, "ruler_stride": r})
+    for d in (4, 8):
+        for c in (128, 256, 512):
+            for r in (16, 32, 64, 128):
+                assert big >= pbit.workspace_size(n, L, 4, {"digit_bits": d, "smem_cutoff": c, "ruler_stride": r})
     assert big >= pbit.workspace_size(n, L, 4)
+
+
+def test_workspace_without_a_digit_width_covers_every_width(so):
+    """A workspace sized with no tune must do for any K the call brings
+    (the digit width follows K): it is at least the size of every width."""
+    from paper_cs_0511020_gb300 import pbit
+    for n, L, kb in ((1 << 20, 1, 4), (1 << 16, 300, 8), (5000, 1, 1)):
+        free = pbit.workspace_size(n, L, kb)
+        for d in range(1, 9):
+            assert free >= pbit.workspace_size(n, L, kb, {"digit_bits": d})
 
 
 _TUNE_PROBE = """
@@ -163,8 +175,9 @@ def test_more_argument_checks_without_a_device(so):
     out = ctypes.c_void_p(0x4000)
     for stage in (0, 3):
         assert L.pbit_debug_stage(ctypes.addressof(pool), 0, 100, 32, 4, stage, None, 0, out, out, None) == pbit.EINVAL
-    # stage 2 needs a list long enough for a global pass
-    assert L.pbit_debug_stage(ctypes.addressof(pool), 0, 100, 32, 4, 2, None, 0, out, out, None) == pbit.EINVAL
+    # stage 2 needs two nodes or more to split
+    one = pbit.Pool(0x1000, 4, 0x2000, 4, 4, 0, 1, 0, 0)
+    assert L.pbit_debug_stage(ctypes.addressof(one), 0, 1, 32, 4, 2, None, 0, out, out, None) == pbit.EINVAL
     assert L.pbit_debug_stage(ctypes.addressof(pool), 0, 100, 32, 4, 1, None, 0, None, out, None) == pbit.EINVAL
     assert L.pbit_debug_stage(ctypes.addressof(pool), 100, 100, 32, 4, 1, None, 0, out, out, None) == pbit.EBADLIST
     assert L.pbit_selftest_bounded_wait(0, None) == pbit.EINVAL

@@ -202,11 +202,7 @@ def test_signed_descending_float(pb, flags):
     st, got, r = _gpu_sort(pb, nxt, key, root, 32, 4, flags=f)
     assert st == pb.OK
     if flags == "float":
-        order_in = O.list_order(nxt, root)
-        v = vals[order_in]
-        # total order of the bit transform: -0.0 sorts before +0.0
-        perm = np.lexsort((np.arange(n), np.signbit(v) == False, v))  # noqa: E712
-        want, wr = O.relink(nxt, order_in[perm])
+        want, wr = O.stable_sort_definition(nxt, key, root, 32, float_keys=True)
     else:
         want, wr = O.stable_sort_definition(nxt, key, root, 32, signed="signed" in flags,
                                             descending="desc" in flags)
@@ -288,10 +284,7 @@ def test_gather_pack_on_and_off(pb, case, pack):
             vals[::7] = 0.0
             key = vals.view(np.uint64)
             flags = pb.FLOAT
-            order_in = O.list_order(nxt, root)
-            v = vals[order_in]
-            perm = np.lexsort((np.arange(n), np.signbit(v) == False, v))  # noqa: E712
-            want, wr = O.relink(nxt, order_in[perm])
+            want, wr = O.stable_sort_definition(nxt, key, root, 64, float_keys=True)
         st, got, r = _gpu_sort(pb, nxt, key, root, 8 * key.itemsize, 4, flags=flags, tune=tune)
         assert st == pb.OK and r == wr and (got == want).all()
         return
@@ -385,10 +378,7 @@ def test_short_list_kernel_variants(pb, variant):
         vals = I.rng(232).standard_normal(n).astype(np.float32)
         vals[::9] = -0.0
         st, got, r = _gpu_sort(pb, nxt, vals.view(np.uint32), root, 32, 4, flags=pb.FLOAT)
-        order_in = O.list_order(nxt, root)
-        v = vals[order_in]
-        perm = np.lexsort((np.arange(n), np.signbit(v) == False, v))  # noqa: E712
-        want, wr = O.relink(nxt, order_in[perm])
+        want, wr = O.stable_sort_definition(nxt, vals.view(np.uint32), root, 32, float_keys=True)
         assert st == pb.OK and r == wr and (got == want).all()
     elif variant == "aos":
         nodes = torch.from_numpy(I.aos_pack(nxt, key)).cuda()
@@ -434,3 +424,45 @@ def test_short_list_kernel_malformed_untouched(pb, case):
     st, _ = pb.sort_pool_list(pb.make_pool(d_next, _dev_key(key)), root, n, 32, 4, check=False)
     assert st == pb.EBADLIST
     assert (d_next.cpu().numpy() == bad).all()
+
+
+def _float_edge_keys(n, width, seed):
+    """Float bit patterns with every class the IEEE order distinguishes:
+    NaNs of both signs (quiet and signaling, several payloads), infinities,
+    both zeros, subnormals of both signs, normals, and repeated patterns."""
+    g = I.rng(seed)
+    dt, ft = (np.uint32, np.float32) if width == 4 else (np.uint64, np.float64)
+    fbits = 23 if width == 4 else 52
+    ebits = 8 if width == 4 else 11
+    sign = dt(1) << dt(8 * width - 1)
+    exp_all = dt((1 << ebits) - 1) << dt(fbits)
+    quiet = dt(1) << dt(fbits - 1)
+    key = (g.standard_normal(n) * 10.0 ** g.integers(-20, 20, n)).astype(ft).view(dt).copy()
+    payload = g.integers(1, 1 << 20, n).astype(dt)
+    key[0::11] = exp_all | quiet | payload[0::11]            # +qNaN
+    key[1::13] = sign | exp_all | quiet | payload[1::13]      # -qNaN
+    key[2::17] = exp_all | (payload[2::17] & (quiet - dt(1)))  # +sNaN
+    key[3::19] = sign | exp_all | (payload[3::19] & (quiet - dt(1)))  # -sNaN
+    key[4::23] = exp_all                                      # +inf
+    key[5::29] = sign | exp_all                               # -inf
+    key[6::31] = 0                                            # +0
+    key[7::37] = sign                                         # -0
+    key[8::41] = payload[8::41]                               # +subnormal
+    key[9::43] = sign | payload[9::43]                        # -subnormal
+    key[10::9] = key[12]                                      # repeated pattern
+    return key
+
+
+@pytest.mark.parametrize("descending", [False, True])
+@pytest.mark.parametrize("width", [4, 8])
+@pytest.mark.parametrize("n", [3001, 120007])
+def test_float_edge_cases_vs_oracle(pb, n, width, descending):
+    """IEEE keys with NaN payloads of both signs, infinities, signed zeros and
+    subnormals against the oracle's totalOrder reading (short-list kernel at
+    3001 nodes, the full pipeline at 120007)."""
+    nxt, root = I.random_list(n, 251 + width)
+    key = _float_edge_keys(n, width, 252 + width)
+    flags = pb.FLOAT | (pb.DESCENDING if descending else 0)
+    st, got, r = _gpu_sort(pb, nxt, key, root, 8 * width, 4, flags=flags)
+    want, wr = O.stable_sort_definition(nxt, key, root, 8 * width, float_keys=True, descending=descending)
+    assert st == pb.OK and r == wr and (got == want).all()
