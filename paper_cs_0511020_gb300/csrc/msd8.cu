@@ -43,62 +43,107 @@ static_assert(k8Bins == k8TPB, "one thread per bucket in the per-tile steps");
 // ------------------------------------------------------------------ hist8
 // For every tile of every pending segment: the counts of the 256 digits of
 // the window [max(hi - D, 0), hi) (row g of tcnt: plain stores), and the
-// AND/OR of the segment's keys (merged per CTA per segment).
+// AND/OR of the segment's keys.  Tiles are dealt round-robin to persistent
+// CTAs; the keys of the next tile are copied into shared memory by the bulk
+// copy engine while the current one is counted.
+struct Hist8Smem {
+    uint32_t h[k8Warps][k8Bins];  // per-warp digit counts
+    unsigned long long s_and, s_or;
+    int32_t seg[2], cnt[2], shk[2], lo[2], hi[2];
+    int32_t cs, ctb_next;         // the issuing thread's segment cursor
+    alignas(8) uint64_t bar[2];
+};
+
+template <typename KeyT>
+struct Hist8Layout {
+    static constexpr int kStage = ((k8Tile * (int)sizeof(KeyT) + 32 + 127) / 128) * 128;
+    static constexpr int kHdr = ((int)sizeof(Hist8Smem) + 127) / 128 * 128;
+    static constexpr int kTotal = kHdr + 2 * kStage;
+};
+
+template <typename KeyT>
+__device__ __forceinline__ void hist8_issue(const Ctx &c, int cur, int P, int g, int st, Hist8Smem &S,
+                                            unsigned char *stage) {
+    while (g >= S.ctb_next) {  // follow the segments forward
+        ++S.cs;
+        S.ctb_next = S.cs + 1 < P ? c.pend_tile_base[cur][S.cs + 1] : INT32_MAX;
+    }
+    const Seg sg = c.pend[cur][S.cs];
+    const int k = g - c.pend_tile_base[cur][S.cs];
+    const int64_t start = (int64_t)sg.start + (int64_t)k * k8Tile;
+    const int cnt = (int)min((int64_t)k8Tile, (int64_t)sg.start + sg.len - start);
+    constexpr int W = (int)sizeof(KeyT);
+    const int64_t k_lo = (start * W) & ~15ll, k_hi = ((start + cnt) * W + 15) & ~15ll;
+    S.seg[st] = S.cs;
+    S.cnt[st] = cnt;
+    S.shk[st] = (int32_t)((start * W - k_lo) / W);
+    S.lo[st] = max(sg.hi - c.D, 0);
+    S.hi[st] = sg.hi;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&S.bar[st], (uint32_t)(k_hi - k_lo));
+    bulk_g2s(stage, c.keyb[sg.buf & 1] + k_lo, (uint32_t)(k_hi - k_lo), &S.bar[st]);
+}
+
 template <typename KeyT>
 __global__ void __launch_bounds__(k8TPB) k_hist8(Ctx c, int it) {
     griddep_wait();
-    __shared__ uint32_t s_h[k8Warps][k8Bins];
-    __shared__ unsigned long long s_and, s_or;
-    __shared__ int s_aseg;
+    extern __shared__ __align__(128) unsigned char smem[];
+    Hist8Smem &S = *reinterpret_cast<Hist8Smem *>(smem);
+    unsigned char *stages = smem + Hist8Layout<KeyT>::kHdr;
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1;
     const int P = c.ctr->pend_count[cur];
-    const int ntiles = c.ctr->stat_tiles[cur];
+    const int T = c.ctr->stat_tiles[cur];
+    const int g0 = blockIdx.x, G = gridDim.x;
+    if (g0 >= T)
+        return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    long long my_elems = 0;
-    for (int w = 0; w < k8Warps; ++w)
-        s_h[w][tid] = 0;
-    if (tid == 0) {
-        s_and = ~0ull;
-        s_or = 0ull;
-        s_aseg = -1;
-    }
     using U = typename KeyWord<KeyT>::U;
-    for (int g = blockIdx.x; g < ntiles; g += gridDim.x) {
-        __syncthreads();  // the previous tile's counts are stored and cleared
-        const int s = upper_index(c.pend_tile_base[cur], P, g);
-        if (tid == 0 && s != s_aseg) {  // AND/OR are merged per segment, not per tile
-            if (s_aseg >= 0) {
-                atomicAnd(&c.pand[cur][s_aseg], s_and);
-                atomicOr(&c.por[cur][s_aseg], s_or);
+    for (int w = 0; w < k8Warps; ++w)
+        S.h[w][tid] = 0;
+    if (tid == 0) {
+        S.s_and = ~0ull;
+        S.s_or = 0ull;
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
+        S.cs = upper_index(c.pend_tile_base[cur], P, g0) - 1;  // the issue steps onto g0's segment
+        S.ctb_next = c.pend_tile_base[cur][S.cs + 1];
+        hist8_issue<KeyT>(c, cur, P, g0, 0, S, stages);
+    }
+    __syncthreads();
+    long long my_elems = 0;
+    uint32_t phases = 0;
+    int st = 0;
+    for (int g = g0; g < T; g += G) {
+        const bool more = g + G < T;
+        if (tid == 0 && more)
+            hist8_issue<KeyT>(c, cur, P, g + G, st ^ 1, S, stages + (st ^ 1) * Hist8Layout<KeyT>::kStage);
+        const bool landed = (tid != 0) || mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
+        if (!__syncthreads_and(landed)) {
+            set_status(c.status, PBIT_ETIMEOUT);
+            if (tid == 0) {  // wait (bounded) for the copies still in flight before leaving
+                mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
+                if (more)
+                    mbar_wait_bounded(&S.bar[st ^ 1], (phases >> (st ^ 1)) & 1u, 1ll << 26);
             }
-            s_and = ~0ull;
-            s_or = 0ull;
-            s_aseg = s;
+            return;
         }
-        __syncthreads();  // the reset precedes this tile's merges
-        const Seg sg = c.pend[cur][s];
-        const int k = g - c.pend_tile_base[cur][s];
-        const int64_t b0 = (int64_t)sg.start + (int64_t)k * k8Tile;
-        const int cnt = (int)min((int64_t)k8Tile, (int64_t)sg.start + sg.len - b0);
-        const KeyT *keys = reinterpret_cast<const KeyT *>(c.keyb[sg.buf & 1]) + b0;
-        const int hi = sg.hi, lo = max(hi - c.D, 0);
-        const unsigned dmask = (1u << (hi - lo)) - 1u;
+        phases ^= 1u << st;
+        const int cnt = S.cnt[st], lo = S.lo[st];
+        const unsigned dmask = (1u << (S.hi[st] - lo)) - 1u;
+        const KeyT *sk = reinterpret_cast<const KeyT *>(stages + st * Hist8Layout<KeyT>::kStage) + S.shk[st];
         my_elems += cnt;
-        U kv[k8Items];
-#pragma unroll
-        for (int u = 0; u < k8Items; ++u) {
-            const int pos = u * k8TPB + tid;
-            kv[u] = pos < cnt ? (U)keys[pos] : (U)0;
-        }
         U w_and = ~(U)0, w_or = 0;
 #pragma unroll
         for (int u = 0; u < k8Items; ++u) {
-            if (u * k8TPB + tid < cnt) {
-                w_and &= kv[u];
-                w_or |= kv[u];
-                atomicAdd(&s_h[wid][(unsigned)(kv[u] >> lo) & dmask], 1u);
+            const int pos = u * k8TPB + tid;
+            if (pos < cnt) {
+                const U kv = (U)sk[pos];
+                w_and &= kv;
+                w_or |= kv;
+                atomicAdd(&S.h[wid][(unsigned)(kv >> lo) & dmask], 1u);
             }
         }
 #pragma unroll
@@ -107,29 +152,31 @@ __global__ void __launch_bounds__(k8TPB) k_hist8(Ctx c, int it) {
             w_or |= __shfl_xor_sync(kFull, w_or, o);
         }
         if (lane == 0) {  // keys are zero-extended to 64 bits
-            atomicAnd(&s_and, (unsigned long long)w_and);
-            atomicOr(&s_or, (unsigned long long)w_or);
+            atomicAnd(&S.s_and, (unsigned long long)w_and);
+            atomicOr(&S.s_or, (unsigned long long)w_or);
         }
         __syncthreads();
         uint32_t sum = 0;
 #pragma unroll
         for (int w = 0; w < k8Warps; ++w) {
-            sum += s_h[w][tid];
-            s_h[w][tid] = 0;
+            sum += S.h[w][tid];
+            S.h[w][tid] = 0;
         }
         if ((int64_t)g < c.row_cap)
             c.tcnt[cur][(int64_t)g * k8Bins + tid] = sum;
         else
             set_status(c.status, kStOverflow);
-    }
-    if (tid == 0) {
-        if (s_aseg >= 0) {
-            atomicAnd(&c.pand[cur][s_aseg], s_and);
-            atomicOr(&c.por[cur][s_aseg], s_or);
+        if (tid == 0) {  // this tile's AND/OR into its segment's
+            atomicAnd(&c.pand[cur][S.seg[st]], S.s_and);
+            atomicOr(&c.por[cur][S.seg[st]], S.s_or);
+            S.s_and = ~0ull;
+            S.s_or = 0ull;
         }
-        if (my_elems)
-            atomicAdd((unsigned long long *)&c.ctr->stat_elems[it], (unsigned long long)my_elems);
+        __syncthreads();  // counters cleared, AND/OR reset, stage free for the copy after next
+        st ^= 1;
     }
+    if (tid == 0 && my_elems)
+        atomicAdd((unsigned long long *)&c.ctr->stat_elems[it], (unsigned long long)my_elems);
 }
 
 // ------------------------------------------------------------- tile_scan8
@@ -192,11 +239,23 @@ __global__ void __launch_bounds__(k8TPB) k_chunk_scan8(Ctx c, int it) {
             h = c.tcnt[cur][(int64_t)c.act[cur][a].row * k8Bins + d];
         } else {
             const int c0 = c.act_chunk_base[cur][a], c1 = c.act_chunk_base[cur][a + 1];
-            for (int ch = c0; ch < c1; ++ch) {
-                uint32_t *p = c.ctot + (int64_t)ch * k8Bins + d;
-                const uint32_t t = *p;
-                *p = h;
-                h += t;
+            uint32_t *col = c.ctot + (int64_t)c0 * k8Bins + d;
+            int ch = 0;
+            for (; ch + 8 <= c1 - c0; ch += 8) {  // eight loads in flight, then the running sum
+                uint32_t x[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    x[u] = col[(int64_t)(ch + u) * k8Bins];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    col[(int64_t)(ch + u) * k8Bins] = h;
+                    h += x[u];
+                }
+            }
+            for (; ch < c1 - c0; ++ch) {
+                const uint32_t x = col[(int64_t)ch * k8Bins];
+                col[(int64_t)ch * k8Bins] = h;
+                h += x;
             }
         }
         int tot;
@@ -206,12 +265,29 @@ __global__ void __launch_bounds__(k8TPB) k_chunk_scan8(Ctx c, int it) {
 }
 
 // ------------------------------------------------------------------ pass8
+// What a CTA needs to know about one tile (written by the thread that issues
+// its copy, read by all after a barrier).
+struct Tile8 {
+    int32_t seg, k, cnt, shk, shi;
+    int32_t start, len, lo, hi, buf, final, row, ch;
+};
+
+// The issuing thread's view of the segment its tiles belong to: tiles are
+// taken in increasing order, so the segment is followed forward.
+struct SegCursor {
+    int s;
+    int32_t tb, tb_next;  // tile bases of segment s and s + 1
+    Seg sg;
+    int32_t ch0;          // first scan chunk of segment s
+};
+
 struct Pass8Smem {
+    int32_t nt[2];                   // the tiles in the two stages (>= num_tiles: none)
     uint32_t wcnt[k8Warps][k8Bins];  // per-warp digit counts -> each warp's first tile slot per digit
     int32_t gdelta[k8Bins];          // output position - tile slot, per digit
     int sh[40];                      // block scan scratch
-    int32_t st_seg[2], st_cnt[2], st_k[2], st_shk[2], st_shi[2];
-    int32_t nt[2];
+    Tile8 tl[2];                     // the tiles in the two stages
+    SegCursor q;                     // the issuing thread's segment cursor
     alignas(8) uint64_t bar[2];
 };
 
@@ -222,16 +298,28 @@ struct Pass8Layout {
     static constexpr int kStage = ((kKeyBytes + kIdxBytes + 127) / 128) * 128;
     static constexpr int kHdr = ((int)sizeof(Pass8Smem) + 127) / 128 * 128;
     static constexpr int kTotal = kHdr + 2 * kStage;
-    static constexpr int kMinBlocks = sizeof(KeyT) == 8 ? 3 : 4;
+    static constexpr int kMinBlocks = 3;  // (at 4 the registers spill: measured slower)
 };
 
-// Issue the bulk copies of tile g into stage st (one thread).
+__device__ __forceinline__ void cursor_seek(const Ctx &c, int cur, int A, int g, SegCursor &q) {
+    if (g < q.tb_next)
+        return;
+    do {
+        ++q.s;
+        q.tb = q.tb_next;
+        q.tb_next = c.act_tile_base[cur][q.s + 1];
+    } while (g >= q.tb_next && q.s + 1 < A);
+    q.sg = c.act[cur][q.s];
+    q.ch0 = c.act_chunk_base[cur][q.s];
+}
+
+// Issue the bulk copies of tile g into stage st and describe the tile (one thread).
 template <typename KeyT>
-__device__ __forceinline__ void pass8_issue(const Ctx &c, int cur, int g, int st, Pass8Smem &S,
-                                            unsigned char *stage, int A) {
-    const int s = upper_index(c.act_tile_base[cur], A, g);
-    const Seg sg = c.act[cur][s];
-    const int k = g - c.act_tile_base[cur][s];
+__device__ __forceinline__ void pass8_issue(const Ctx &c, int cur, int A, int g, int st, SegCursor &q, Pass8Smem &S,
+                                            unsigned char *stage) {
+    cursor_seek(c, cur, A, g, q);
+    const Seg &sg = q.sg;
+    const int k = g - q.tb;
     const int64_t start = (int64_t)sg.start + (int64_t)k * k8Tile;
     const int cnt = (int)min((int64_t)k8Tile, (int64_t)sg.start + sg.len - start);
     constexpr int W = (int)sizeof(KeyT);
@@ -241,25 +329,47 @@ __device__ __forceinline__ void pass8_issue(const Ctx &c, int cur, int g, int st
     // carry 64 bytes of slack behind their end for the rounding up
     const int64_t k_lo = (start * W) & ~15ll, k_hi = ((start + cnt) * W + 15) & ~15ll;
     const int64_t i_lo = (start * 4) & ~15ll, i_hi = ((start + cnt) * 4 + 15) & ~15ll;
-    S.st_seg[st] = s;
-    S.st_cnt[st] = cnt;
-    S.st_k[st] = k;
-    S.st_shk[st] = (int32_t)((start * W - k_lo) / W);
-    S.st_shi[st] = (int32_t)((start * 4 - i_lo) / 4);
+    Tile8 &t = S.tl[st];
+    t.seg = q.s;
+    t.k = k;
+    t.cnt = cnt;
+    t.shk = (int32_t)((start * W - k_lo) / W);
+    t.shi = (int32_t)((start * 4 - i_lo) / 4);
+    t.start = sg.start;
+    t.len = sg.len;
+    t.lo = sg.lo;
+    t.hi = sg.hi;
+    t.buf = sg.buf;
+    t.final = sg.final;
+    t.row = sg.row;
+    t.ch = q.ch0 + k / kScanChunk;
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(&S.bar[st], (uint32_t)((k_hi - k_lo) + (i_hi - i_lo)));
     bulk_g2s(stage, kb + k_lo, (uint32_t)(k_hi - k_lo), &S.bar[st]);
     bulk_g2s(stage + Pass8Layout<KeyT>::kKeyBytes, ib + i_lo, (uint32_t)(i_hi - i_lo), &S.bar[st]);
 }
 
-// Persistent CTAs take tiles from a counter; the bulk copy of the next tile
-// is in flight while the current one is ranked and written.  Ranking: for
-// each 32-element group a warp finds, with one ballot per digit bit, the
-// lanes holding the same digit (peers); the lowest of them adds the group's
-// count to the warp's shared counter of that digit and passes the old value
-// to its peers, so every element learns how many elements with its digit
-// came before it in the warp's part of the tile (memory order = warp, group,
-// lane: the order is stable).
+// Output position of the tile's first element of digit d: bucket start +
+// the digit's count in the segment's earlier tiles.
+__device__ __forceinline__ int32_t tile_base8(const Ctx &c, int cur, const Tile8 &t, int d) {
+    int32_t gb = t.start + (int32_t)c.act_hist[cur][(int64_t)t.seg * k8Bins + d];
+    if (t.k > 0)
+        gb += (int32_t)(c.ctot[(int64_t)t.ch * k8Bins + d] + c.tcnt[cur][((int64_t)t.row + t.k) * k8Bins + d]);
+    return gb;
+}
+
+// Persistent CTAs claim tiles from a counter; the bulk copy of the next tile
+// is in flight, and the output bases of its digits are being loaded, while
+// the current one is ranked and written.  Ranking: for each 32-element group
+// a warp finds the lanes holding the same digit (peers); the lowest of them
+// adds the group's count to the warp's shared counter of that digit and
+// passes the old value to its peers, so
+// every element learns how many elements with its digit came before it in
+// the warp's part of the tile (memory order = warp, group, lane: the order
+// is stable).  Peers come from eight ballots, one per digit bit: a lane keeps
+// the lanes that differ from it in no bit.  (The match instruction finds the
+// same lanes in one instruction, but measured on this GPU it saturated the
+// ADU pipe at 81% and the pass ran 5% slower than with ballots.)
 template <typename KeyT>
 __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(Ctx c, int it) {
     griddep_wait();
@@ -272,63 +382,69 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned lt = lanemask_lt();
     const int A = c.ctr->act_count[cur];
-    const int ntiles = c.ctr->num_tiles[cur];
-    if (A == 0 || ntiles == 0)
+    const int T = c.ctr->num_tiles[cur];
+    if (A == 0 || T == 0)
         return;
+    // Tiles are claimed from a counter one step ahead (the claim's latency
+    // hides behind a tile), so the tiles in flight at one time are
+    // neighbours: the runs they write into each bucket are neighbours too and
+    // fill whole lines while they are still in L2.  A CTA's claims increase,
+    // so its thread 0 follows the segments forward.
+    SegCursor &q = S.q;  // used by thread 0 only
+    int claim = 0;       // thread 0: the tile claimed for the next issue
     if (tid == 0) {
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         fence_mbar_init();
+        const int g0 = atomicAdd(&c.ctr->tile_ctr[it], 1);
+        S.nt[0] = g0;
+        if (g0 < T) {
+            q.s = upper_index(c.act_tile_base[cur], A, g0) - 1;  // the seek below steps onto g0's segment
+            q.tb_next = c.act_tile_base[cur][q.s + 1];
+            q.tb = q.tb_next;
+            pass8_issue<KeyT>(c, cur, A, g0, 0, q, S, stages);
+            claim = atomicAdd(&c.ctr->tile_ctr[it], 1);
+        }
     }
 #pragma unroll
     for (int w = 0; w < k8Warps; ++w)
         S.wcnt[w][tid] = 0;
-    uint32_t phases = 0;  // bit b: parity of stage b's barrier
-    int st = 0;
-    if (tid == 0) {
-        const int g = atomicAdd(&c.ctr->tile_ctr[it], 1);
-        S.nt[0] = g;
-        if (g < ntiles)
-            pass8_issue<KeyT>(c, cur, g, 0, S, stages, A);
-    }
     __syncthreads();
     int g = S.nt[0];
-    while (g < ntiles) {
+    if (g >= T)
+        return;
+    int32_t gb = tile_base8(c, cur, S.tl[0], tid);
+    uint32_t phases = 0;  // bit b: parity of stage b's barrier
+    int st = 0;
+    while (g < T) {
         unsigned char *stage = stages + st * Pass8Layout<KeyT>::kStage;
-        if (tid == 0) {  // prefetch the next tile into the other stage
-            const int g2 = atomicAdd(&c.ctr->tile_ctr[it], 1);
-            S.nt[st ^ 1] = g2;
-            if (g2 < ntiles)
-                pass8_issue<KeyT>(c, cur, g2, st ^ 1, S, stages + (st ^ 1) * Pass8Layout<KeyT>::kStage, A);
-        }
-        const int s = S.st_seg[st];
-        const int k = S.st_k[st];
-        const int cnt = S.st_cnt[st];
-        const Seg sg = c.act[cur][s];
-        const int lo = sg.lo, width = sg.hi - sg.lo;
-        const unsigned dmask = (1u << width) - 1u;
-        // output position of this tile's first element of digit tid: bucket
-        // start + the digit's count in the segment's earlier tiles (loads in
-        // flight while the copy lands)
-        int32_t gb = sg.start + (int32_t)c.act_hist[cur][(int64_t)s * k8Bins + tid];
-        if (k > 0) {
-            const int ch = c.act_chunk_base[cur][s] + k / kScanChunk;
-            gb += (int32_t)(c.ctot[(int64_t)ch * k8Bins + tid] + c.tcnt[cur][((int64_t)sg.row + k) * k8Bins + tid]);
+        if (tid == 0) {  // prefetch the next tile into the other stage, claim the one after
+            S.nt[st ^ 1] = claim;
+            if (claim < T) {
+                pass8_issue<KeyT>(c, cur, A, claim, st ^ 1, q, S, stages + (st ^ 1) * Pass8Layout<KeyT>::kStage);
+                claim = atomicAdd(&c.ctr->tile_ctr[it], 1);
+            }
         }
         // one thread waits for the copy (acquire), the barrier publishes it
+        // (and the next tile's description)
         const bool landed = (tid != 0) || mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
         if (!__syncthreads_and(landed)) {
             set_status(c.status, PBIT_ETIMEOUT);
             if (tid == 0) {  // wait (bounded) for the copies still in flight before leaving
                 mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
-                if (S.nt[st ^ 1] < ntiles)
+                if (S.nt[st ^ 1] < T)
                     mbar_wait_bounded(&S.bar[st ^ 1], (phases >> (st ^ 1)) & 1u, 1ll << 26);
             }
             return;
         }
         phases ^= 1u << st;
-        const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + S.st_shk[st];
-        const int32_t *si = reinterpret_cast<const int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes) + S.st_shi[st];
+        const int gnext = S.nt[st ^ 1];
+        const bool more = gnext < T;
+        const Tile8 &t = S.tl[st];  // (fields read from shared memory where used)
+        const int lo = t.lo, cnt = t.cnt;
+        const unsigned dmask = (1u << (t.hi - t.lo)) - 1u;
+        const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + t.shk;
+        const int32_t *si = reinterpret_cast<const int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes) + t.shi;
 
         // ---- ranking within the warp
         KeyT key[k8Items];
@@ -342,14 +458,15 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
             key[i] = valid ? sk[pos] : (KeyT)0;
             idx[i] = valid ? si[pos] : 0;
             const unsigned dig = digit_of<KeyT>(key[i], lo, dmask);
-            unsigned peers = __ballot_sync(kFull, valid);
+            // peers: the valid lanes that differ from this one in no digit
+            // bit (bits above a narrower window are 0 everywhere)
+            unsigned diff = 0;
 #pragma unroll
             for (int b = 0; b < k8Bits; ++b) {
-                if (b < width) {  // warp-uniform
-                    const unsigned bb = __ballot_sync(kFull, (dig >> b) & 1u);
-                    peers &= ((dig >> b) & 1u) ? bb : ~bb;
-                }
+                const int m = (int)(dig << (31 - b)) >> 31;  // -1 if bit b is set, else 0
+                diff |= __ballot_sync(kFull, m != 0) ^ (unsigned)m;
             }
+            const unsigned peers = __ballot_sync(kFull, valid) & ~diff;
             const int leader = __ffs(peers) - 1;  // (an invalid lane's value is never used)
             uint32_t before = 0;
             if (valid && lane == leader)
@@ -357,6 +474,8 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
             rnk[i] = __shfl_sync(kFull, before, leader & 31) + (uint32_t)__popc(peers & lt);
         }
         __syncthreads();
+        // the next tile's output bases: loads in flight during the rest of this tile
+        const int32_t gb_next = more ? tile_base8(c, cur, S.tl[st ^ 1], tid) : 0;
         // ---- tile offsets per digit (thread tid = digit), each warp's first slot
         {
             uint32_t cw[k8Warps];
@@ -393,28 +512,28 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
         for (int w = 0; w < k8Warps; ++w)  // counters of the next tile
             S.wcnt[w][tid] = 0;
         // ---- coalesced write-out: slot j goes to gdelta[its digit] + j
-        if (lo == 0 || sg.final) {
+        if (lo == 0 || t.final) {
 #pragma unroll
             for (int u = 0; u < k8Items; ++u) {
                 const int j = u * k8TPB + tid;
                 if (j < cnt) {
                     const int dst = S.gdelta[digit_of<KeyT>(ok[j], lo, dmask)] + j;
-                    if ((unsigned)(dst - sg.start) >= (unsigned)sg.len)
+                    if ((unsigned)(dst - t.start) >= (unsigned)t.len)
                         set_status(c.status, kStOverflow);
                     else
                         c.F[dst] = oi[j];
                 }
             }
         } else {
-            KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(sg.buf & 1) ^ 1]);
-            int32_t *oidx = c.idxb[(sg.buf & 1) ^ 1];
+            KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(t.buf & 1) ^ 1]);
+            int32_t *oidx = c.idxb[(t.buf & 1) ^ 1];
 #pragma unroll
             for (int u = 0; u < k8Items; ++u) {
                 const int j = u * k8TPB + tid;
                 if (j < cnt) {
                     const KeyT kk = ok[j];
                     const int dst = S.gdelta[digit_of<KeyT>(kk, lo, dmask)] + j;
-                    if ((unsigned)(dst - sg.start) >= (unsigned)sg.len) {
+                    if ((unsigned)(dst - t.start) >= (unsigned)t.len) {
                         set_status(c.status, kStOverflow);
                     } else {
                         okey[dst] = kk;
@@ -424,7 +543,8 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
             }
         }
         __syncthreads();
-        g = S.nt[st ^ 1];
+        gb = gb_next;
+        g = gnext;
         st ^= 1;
     }
 }
@@ -573,7 +693,12 @@ static void launch_iter8_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     const int per_sm = Pass8Layout<KeyT>::kMinBlocks;
     const unsigned wblocks = (unsigned)max(1, min(sms * 8, (int)((c.seg_cap + 7) / 8)));  // 8 warps per CTA
     const unsigned sblocks = (unsigned)max(1, min(sms * 8, (int)c.seg_cap));
-    launch_pdl(k_hist8<KeyT>, dim3(sms * 8), dim3(k8TPB), 0, s, c, it);
+    {
+        const int hsmem = Hist8Layout<KeyT>::kTotal;
+        cudaFuncSetAttribute(k_hist8<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, hsmem);
+        const int per_sm = max(1, min(8, (200 * 1024) / (hsmem + 1024)));
+        launch_pdl(k_hist8<KeyT>, dim3(sms * per_sm), dim3(k8TPB), hsmem, s, c, it);
+    }
     prof_mark("seg_stats", s);
     launch_plan_pending(c, it, s);
     launch_pdl(k_tile_scan8, dim3(sms * 4), dim3(k8TPB), 0, s, c, it);
