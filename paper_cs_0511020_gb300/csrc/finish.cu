@@ -329,217 +329,214 @@ __global__ void __launch_bounds__(32 * kFWarps) k_finish(Ctx c) {
 }
 
 // Mid-size buckets (more than the warp finish takes, at most kMidCap nodes,
-// with at most kMidSpan varying key bits): one CTA per bucket.  The bucket
-// is loaded once into shared memory and sorted there least significant
-// window first over the bits that vary in it (windows of up to 4 bits spread
-// evenly over the varying span).  In each window every warp takes one
-// contiguous slice of the bucket (up to kMidG groups of 32) into registers
-// and ranks all its groups at once with one ballot per digit bit: a lane
-// learns the lanes of its group holding its digit, and lane d the group's
-// count of digit d, summed over the groups in registers.  Warp 0 turns the
-// (warp, digit) totals into each warp's first slot per digit (digit-major,
-// warps in slice order, so the order is stable), and every element goes to
-// (its warp's slot for its digit) + (its digit's count in earlier groups of
-// the slice) + (its peers in lower lanes) in the other buffer.  This replaces
-// the further global passes, their planning and the small-bucket finish that
-// such a bucket would otherwise go through.
-constexpr int kMidTPB = 512;
+// with at most kMidSpan varying key bits): one CTA per bucket.  The bulk copy
+// engine loads the bucket into shared memory; the CTA sorts it there, least
+// significant window first, on windows of up to 8 bits spread evenly over the
+// bits that vary in it (one window for spans up to 8 bits, two up to 16),
+// and writes the node ids to F.  A window is a stable counting split: each
+// warp ranks its contiguous slice of the bucket group by group (32 elements:
+// the lanes holding the same digit are found with one ballot per digit bit,
+// the lowest of them adds the group's count to the warp's shared counter of
+// that digit and passes the old value on), one thread per digit then turns
+// the (warp, digit) counts into each warp's first slot (digit-major, warps in
+// slice order: stable), and every element moves to its slot in the other
+// buffer.  This replaces the further global passes, their planning and the
+// small-bucket finish that such a bucket would otherwise go through.
+constexpr int kMidTPB = 256;
 constexpr int kMidWarps = kMidTPB / 32;
-constexpr int kMidG = kMidCap / kMidTPB;  // groups per warp slice
-static_assert(kMidG * kMidTPB == kMidCap, "slices cover the bucket");
+constexpr int kMidItems = kMidCap / kMidTPB;  // groups of 32 per warp slice, at most
+constexpr int kMidBits = 8;
+constexpr int kMidBins = 1 << kMidBits;
+static_assert(kMidBins == kMidTPB, "one thread per digit");
 
 template <typename KeyT>
 struct MidLayout {
-    static constexpr int kKeyBuf = kMidCap * (int)sizeof(KeyT);
-    static constexpr int kIdxBuf = kMidCap * 4;
-    static constexpr int kTotal = 2 * kKeyBuf + 2 * kIdxBuf;
+    static constexpr int kKeyBuf = kMidCap * (int)sizeof(KeyT) + 32;  // + room for the copy's 16-byte rounding
+    static constexpr int kIdxBuf = kMidCap * 4 + 32;
+    static constexpr int kBuf = ((kKeyBuf + kIdxBuf + 127) / 128) * 128;
+    static constexpr int kTotal = 2 * kBuf;
+    static constexpr int kMinBlocks = sizeof(KeyT) == 8 ? 2 : 3;
+};
+
+struct MidSmem {
+    uint32_t wcnt[kMidWarps][kMidBins];
+    int sh[40];
+    unsigned long long s_and, s_or;
+    int32_t next;  // bucket claimed next
+    alignas(8) uint64_t bar;
 };
 
 template <typename KeyT>
-__global__ void __launch_bounds__(kMidTPB, 2) k_finish_mid(Ctx c) {
+__global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish_mid(Ctx c) {
     griddep_wait();
-    extern __shared__ __align__(16) unsigned char msm[];
+    extern __shared__ __align__(128) unsigned char msm[];
+    __shared__ MidSmem S;
     using U = typename KeyWord<KeyT>::U;
     using L = MidLayout<KeyT>;
-    __shared__ uint32_t s_cnt[kMidWarps][kFBins];  // per (warp, digit): count -> first slot
-    __shared__ uint32_t s_dig[kFBins + 1];          // split: first slot of each digit, then len
-    __shared__ int s_split;
-    __shared__ U s_and[kMidWarps], s_or[kMidWarps];
     if (*(volatile int32_t *)c.status)
         return;
-    KeyT *skey = reinterpret_cast<KeyT *>(msm);                         // [2][kMidCap]
-    int32_t *sidx = reinterpret_cast<int32_t *>(msm + 2 * L::kKeyBuf);  // [2][kMidCap]
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned lt = lanemask_lt();
     const int nmid = c.ctr->mid_count;
+    unsigned char *bufA = msm, *bufB = msm + L::kBuf;
+    if (tid == 0) {
+        mbar_init(&S.bar, 1);
+        fence_mbar_init();
+        S.next = atomicAdd(&c.ctr->fin_ctr.v, 1);
+    }
+#pragma unroll
+    for (int w = 0; w < kMidWarps; ++w)
+        S.wcnt[w][tid] = 0;
+    __syncthreads();
+    uint32_t phase = 0;
     long long my_elems = 0;
-    for (int m = blockIdx.x; m < nmid; m += gridDim.x) {
+    for (int m = S.next; m < nmid; m = S.next) {
         const Fin f = c.mid[m];
         const int len = f.len, hi = f.hi;
-        if (len > kMidCap || len < 0) {
+        const bool ok_len = len > 0 && len <= kMidCap;
+        constexpr int W = (int)sizeof(KeyT);
+        int shk = 0, shi = 0;
+        {
+            const int64_t start = f.start;
+            const int64_t k_lo = (start * W) & ~15ll, k_hi = ((start + len) * W + 15) & ~15ll;
+            const int64_t i_lo = (start * 4) & ~15ll, i_hi = ((start + len) * 4 + 15) & ~15ll;
+            shk = (int)((start * W - k_lo) / W);
+            shi = (int)((start * 4 - i_lo) / 4);
+            if (tid == 0 && ok_len) {
+                const int buf = f.mode_buf & 1;
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(&S.bar, (uint32_t)((k_hi - k_lo) + (i_hi - i_lo)));
+                bulk_g2s(bufA, c.keyb[buf] + k_lo, (uint32_t)(k_hi - k_lo), &S.bar);
+                bulk_g2s(bufA + L::kKeyBuf, reinterpret_cast<const unsigned char *>(c.idxb[buf]) + i_lo,
+                         (uint32_t)(i_hi - i_lo), &S.bar);
+            }
+        }
+        if (tid == 0) {
+            S.s_and = ~0ull;
+            S.s_or = 0ull;
+        }
+        const bool landed = (tid != 0) || !ok_len || mbar_wait_bounded(&S.bar, phase, 1ll << 26);
+        if (!__syncthreads_and(landed)) {
+            set_status(c.status, PBIT_ETIMEOUT);
+            if (tid == 0)  // wait (bounded) for the copy in flight before leaving
+                mbar_wait_bounded(&S.bar, phase, 1ll << 26);
+            return;
+        }
+        if (tid == 0)  // every thread has read m: claim the next bucket
+            S.next = atomicAdd(&c.ctr->fin_ctr.v, 1);
+        if (!ok_len) {  // (a planning error: cannot happen)
             set_status(c.status, kStOverflow);
+            __syncthreads();
             continue;
         }
+        phase ^= 1u;
         my_elems += len;
-        const int buf = f.mode_buf & 1;
-        const KeyT *src_key = reinterpret_cast<const KeyT *>(c.keyb[buf]) + f.start;
-        const int32_t *src_idx = c.idxb[buf] + f.start;
-        U a_and = ~(U)0, a_or = 0;
-        for (int e = tid; e < len; e += kMidTPB) {
-            const KeyT k = src_key[e];
-            skey[e] = k;
-            sidx[e] = src_idx[e];
-            a_and &= (U)k;
-            a_or |= (U)k;
-        }
+        // the bits that vary in the bucket
+        KeyT *ka = reinterpret_cast<KeyT *>(bufA) + shk;
+        int32_t *ia = reinterpret_cast<int32_t *>(bufA + L::kKeyBuf) + shi;
+        KeyT *kb = reinterpret_cast<KeyT *>(bufB);
+        int32_t *ib = reinterpret_cast<int32_t *>(bufB + L::kKeyBuf);
+        {
+            U a_and = ~(U)0, a_or = 0;
+            for (int e = tid; e < len; e += kMidTPB) {
+                const U k = (U)ka[e];
+                a_and &= k;
+                a_or |= k;
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a_and &= __shfl_xor_sync(kFull, a_and, o);
-            a_or |= __shfl_xor_sync(kFull, a_or, o);
-        }
-        if (lane == 0) {
-            s_and[wid] = a_and;
-            s_or[wid] = a_or;
+            for (int o = 16; o > 0; o >>= 1) {
+                a_and &= __shfl_xor_sync(kFull, a_and, o);
+                a_or |= __shfl_xor_sync(kFull, a_or, o);
+            }
+            if (lane == 0) {
+                atomicAnd(&S.s_and, (unsigned long long)a_and);
+                atomicOr(&S.s_or, (unsigned long long)a_or);
+            }
         }
         __syncthreads();
-        a_and = ~(U)0;
-        a_or = 0;
-#pragma unroll
-        for (int w = 0; w < kMidWarps; ++w) {
-            a_and &= s_and[w];
-            a_or |= s_or[w];
-        }
-        const unsigned long long vary =
-            (unsigned long long)(a_and ^ a_or) & (hi >= 64 ? ~0ull : ((1ull << hi) - 1ull));
-        // each warp owns a contiguous slice of whole 32-element groups
-        const int ngr = (len + 31) >> 5;
-        const int gpw = (ngr + kMidWarps - 1) / kMidWarps;  // <= kMidG
-        const int s0 = min(len, wid * gpw * 32), s1 = min(len, (wid + 1) * gpw * 32);
-        int a = 0;
+        const unsigned long long vary = (S.s_and ^ S.s_or) & (hi >= 64 ? ~0ull : ((1ull << hi) - 1ull));
+        const int32_t *res = ia;  // node ids in final order
         if (vary) {
             const int lv = __ffsll((long long)vary) - 1, hv = 63 - __clzll((long long)vary);
             const int span = hv - lv + 1;
-            // First try one most-significant split on the top 4 varying bits,
-            // whose sub-buckets the warps then finish with the register
-            // network; else (a sub-bucket too large, or its network key too
-            // wide) least significant windows over the whole span.
-            const int split_lo = hv + 1 - kFD;
-            bool try_split = span > kFD && split_lo + 9 <= 32;
-            const int nwin = (span + kFD - 1) / kFD;
-            const int width0 = (span + nwin - 1) / nwin;
-            int wl = try_split ? split_lo : lv;
-            while (wl <= hv && (vary >> wl) != 0) {  // block-uniform
-                if (!try_split)
-                    wl += __ffsll((long long)(vary >> wl)) - 1;
-                const int width = try_split ? kFD : min(width0, hi - wl);
-                const unsigned dmask = (1u << width) - 1u;
-                const KeyT *ka = skey + a * kMidCap;
-                const int32_t *ia = sidx + a * kMidCap;
-                KeyT *kb = skey + (a ^ 1) * kMidCap;
-                int32_t *ib = sidx + (a ^ 1) * kMidCap;
-                KeyT k[kMidG];
-                int32_t x[kMidG];
-                unsigned dig[kMidG], peers[kMidG];
-                uint32_t before[kMidG];  // lane d: count of digit d in earlier groups of the slice
-                uint32_t tot = 0;
+            const int nwin = (span + kMidBits - 1) / kMidBits;
+            const int width = (span + nwin - 1) / nwin;
+            const int nitems = (len + kMidTPB - 1) / kMidTPB;  // groups per warp slice
+            const int s0 = wid * 32 * nitems;
+            for (int w = 0; w < nwin; ++w) {
+                const int wl = lv + w * width;
+                const unsigned dmask = (1u << min(width, hv + 1 - wl)) - 1u;
+                const bool last = w == nwin - 1;
+                uint32_t rnk[kMidItems];
 #pragma unroll
-                for (int g = 0; g < kMidG; ++g) {
-                    const int pos = s0 + g * 32 + lane;
-                    const bool valid = g < gpw && pos < s1;
-                    k[g] = 0;
-                    x[g] = 0;
-                    dig[g] = 0;
-                    peers[g] = 0;
-                    before[g] = tot;
-                    if (g < gpw) {  // warp-uniform
-                        if (valid) {
-                            k[g] = ka[pos];
-                            x[g] = ia[pos];
-                            dig[g] = digit_of<KeyT>(k[g], wl, dmask);
+                for (int i = 0; i < kMidItems; ++i) {
+                    rnk[i] = 0;
+                    if (i < nitems) {  // warp-uniform
+                        const int pos = s0 + i * 32 + lane;
+                        const bool valid = pos < len;
+                        const unsigned dig = valid ? digit_of<KeyT>(ka[pos], wl, dmask) : 0u;
+                        unsigned diff = 0;
+#pragma unroll
+                        for (int b = 0; b < kMidBits; ++b) {
+                            const int mb = (int)(dig << (31 - b)) >> 31;  // -1 if bit b is set, else 0
+                            diff |= __ballot_sync(kFull, mb != 0) ^ (unsigned)mb;
                         }
-                        unsigned pm = __ballot_sync(kFull, valid), mine = pm;
-#pragma unroll
-                        for (int bit = 0; bit < kFD; ++bit) {
-                            if (bit < width) {
-                                const unsigned bb = __ballot_sync(kFull, (dig[g] >> bit) & 1u);
-                                pm &= ((dig[g] >> bit) & 1u) ? bb : ~bb;
-                                mine &= ((lane >> bit) & 1) ? bb : ~bb;
-                            }
-                        }
-                        peers[g] = pm;
-                        tot += (uint32_t)__popc(mine);
-                    }
-                }
-                if (lane < kFBins)
-                    s_cnt[wid][lane] = (unsigned)lane <= dmask ? tot : 0u;
-                __syncthreads();
-                if (wid == 0 && lane < kFBins) {  // slots: digit-major, warps in slice order
-                    uint32_t dtot = 0;
-#pragma unroll
-                    for (int w = 0; w < kMidWarps; ++w)
-                        dtot += s_cnt[w][lane];
-                    uint32_t incl = dtot;
-#pragma unroll
-                    for (int o = 1; o < kFBins; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffu, incl, o);
-                        if (lane >= o)
-                            incl += y;
-                    }
-                    uint32_t run = incl - dtot;
-                    s_dig[lane] = run;
-                    const bool big = __any_sync(0xffffu, dtot > (uint32_t)kNetMax);
-                    if (lane == 0) {
-                        s_dig[kFBins] = (uint32_t)len;
-                        s_split = try_split && !big;
-                    }
-#pragma unroll
-                    for (int w = 0; w < kMidWarps; ++w) {
-                        const uint32_t v = s_cnt[w][lane];
-                        s_cnt[w][lane] = run;
-                        run += v;
+                        const unsigned peers = __ballot_sync(kFull, valid) & ~diff;
+                        const int leader = __ffs(peers) - 1;
+                        uint32_t before = 0;
+                        if (valid && lane == leader)
+                            before = atomicAdd(&S.wcnt[wid][dig], (uint32_t)__popc(peers));
+                        rnk[i] = __shfl_sync(kFull, before, leader & 31) + (uint32_t)__popc(peers & lt);
                     }
                 }
                 __syncthreads();
-                if (try_split && !s_split) {  // block-uniform: fall back to LSD windows
-                    try_split = false;
-                    wl = lv;
-                    continue;
-                }
-                const uint32_t wfirst = lane < kFBins ? s_cnt[wid][lane] : 0u;
+                {  // each warp's first slot per digit (thread tid = digit)
+                    uint32_t cw[kMidWarps];
+                    uint32_t tot = 0;
 #pragma unroll
-                for (int g = 0; g < kMidG; ++g) {
-                    if (g < gpw) {
-                        const uint32_t p = __shfl_sync(kFull, wfirst + before[g], (int)dig[g]) +
-                                           (uint32_t)__popc(peers[g] & lt);
-                        if (s0 + g * 32 + lane < s1) {
-                            kb[p] = k[g];
-                            ib[p] = x[g];
+                    for (int x = 0; x < kMidWarps; ++x) {
+                        cw[x] = S.wcnt[x][tid];
+                        tot += cw[x];
+                    }
+                    int ttot;
+                    uint32_t run = (uint32_t)block_excl_scan((int)tot, &ttot, S.sh);
+#pragma unroll
+                    for (int x = 0; x < kMidWarps; ++x) {
+                        S.wcnt[x][tid] = run;
+                        run += cw[x];
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (int i = 0; i < kMidItems; ++i) {
+                    if (i < nitems) {
+                        const int pos = s0 + i * 32 + lane;
+                        if (pos < len) {
+                            const KeyT k = ka[pos];
+                            const uint32_t p = S.wcnt[wid][digit_of<KeyT>(k, wl, dmask)] + rnk[i];
+                            if (!last)
+                                kb[p] = k;
+                            ib[p] = ia[pos];
                         }
                     }
                 }
                 __syncthreads();
-                a ^= 1;
-                if (try_split)
-                    break;
-                wl += width;
-            }
-            if (try_split) {  // finish the sub-buckets of the split: one warp each
-                int32_t *dst = c.F + f.start;
-                for (int d = wid; d < kFBins; d += kMidWarps) {
-                    const int o = (int)s_dig[d], n = (int)s_dig[d + 1] - o;
-                    if (n > 0 && !net_finish<KeyT>(skey + a * kMidCap + o, sidx + a * kMidCap + o, dst + o, n,
-                                                   split_lo, lane))
-                        set_status(c.status, kStOverflow);  // excluded above: cannot happen
-                }
-                __syncthreads();  // the buffers are reused by the next bucket
-                continue;
+#pragma unroll
+                for (int x = 0; x < kMidWarps; ++x)  // counters of the next window
+                    S.wcnt[x][tid] = 0;
+                res = ib;
+                KeyT *tk = ka;  // the other buffer is the next window's source
+                ka = kb;
+                kb = tk;
+                int32_t *ti = ia;
+                ia = ib;
+                ib = ti;
             }
         }
-        const int32_t *ia = sidx + a * kMidCap;
         int32_t *dst = c.F + f.start;
         for (int e = tid; e < len; e += kMidTPB)
-            dst[e] = ia[e];
-        __syncthreads();  // the buffers are reused by the next bucket
+            dst[e] = res[e];
+        __syncthreads();  // the buffers and counters are reused by the next bucket
     }
     if (tid == 0 && my_elems)  // every thread counted the same buckets
         atomicAdd((unsigned long long *)&c.ctr->fin_sort_elems, (unsigned long long)my_elems);
@@ -809,7 +806,10 @@ static void launch_finish_t(const Ctx &c, cudaStream_t s, int sms) {
     {
         const int smem = MidLayout<KeyT>::kTotal;
         cudaFuncSetAttribute(k_finish_mid<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        const int per_sm = max(1, min(4, (220 * 1024) / (smem + 2048)));
+        const int per_sm = MidLayout<KeyT>::kMinBlocks;  // (registers and shared memory allow this many)
+        static_assert(3 * (MidLayout<uint32_t>::kTotal + (int)sizeof(MidSmem) + 1024) <= 228 * 1024, "3 CTAs per SM");
+        static_assert(2 * (MidLayout<unsigned long long>::kTotal + (int)sizeof(MidSmem) + 1024) <= 228 * 1024,
+                      "2 CTAs per SM");
         launch_pdl(k_finish_mid<KeyT>, dim3((unsigned)(sms * per_sm)), dim3(kMidTPB), smem, s, c);
     }
     const int smem = (int)(kFWarps * 2 * kFinCap * (sizeof(KeyT) + 4));
