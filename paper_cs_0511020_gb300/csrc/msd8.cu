@@ -369,7 +369,8 @@ __device__ __forceinline__ int32_t tile_base8(const Ctx &c, int cur, const Tile8
 // is stable).  Peers come from eight ballots, one per digit bit: a lane keeps
 // the lanes that differ from it in no bit.  (The match instruction finds the
 // same lanes in one instruction, but measured on this GPU it saturated the
-// ADU pipe at 81% and the pass ran 5% slower than with ballots.)
+// ADU pipe at 81% and the pass ran slower than with ballots, also when only
+// every second or every fourth group used it.)
 template <typename KeyT>
 __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(Ctx c, int it) {
     griddep_wait();
