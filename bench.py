@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-list batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-serving leg")
     ap.add_argument("--batched-lists", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=2000, help="timed requests of the serving leg")
-    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-requests", type=int, default=20000, help="timed requests of each serving trace")
+    ap.add_argument("--serve-warmup", type=int, default=1000)
+    ap.add_argument("--serve-pools", type=int, default=1000, help="device pools the request stream cycles through")
     return ap.parse_args()
 
 
@@ -442,79 +443,149 @@ def run_batched(a, torch, pbit, I, local=0):
 
 
 def run_serve(a, torch, pbit, I, local=0):
-    """Serving workload: open-loop Poisson arrivals (mean gap 0.5 ms), lengths
-    log-uniform in [2^4, 2^24], key widths 2/4/8 bytes in 1:2:1 (M = 8 x
-    width), pools resident on the device, 16 GB admission budget.  Latency =
-    completion seen by the scheduler - scheduled arrival (host monotonic
-    clock).  The same trace is then served FIFO, one synchronous
-    pbit_sort_list call at a time."""
-    R = a.serve_warmup + a.serve_requests
-    arr, lens, kbs = I.config5_requests(R, I.SEED_BASE + 5)  # arrival times (s), lengths, key widths
+    """Serving workload: open-loop Poisson arrivals, lengths log-uniform in
+    [2^4, 2^24], key widths 2/4/8 bytes in 1:2:1 (M = 8 x width), uniform keys,
+    random order, pools resident on the device, 16 GB admission budget.  Two
+    traces: the request rate of the workload (mean gap 0.5 ms) and a
+    saturating one (mean gap 0.1 ms, above what either arm can serve).  Each
+    runs `--serve-requests` timed requests after `--serve-warmup` through a
+    ring of `--serve-pools` device pools: request i sorts pool i mod P, and a
+    pool is restored from its saved next[] on a side stream as soon as its
+    request completes (before its next use; the copies share the GPU with the
+    sorts in both arms).  Served arm: pbit_serve_*; FIFO arm: one synchronous
+    pbit_sort_list call per request, in arrival order.  Latency = completion
+    (seen by the scheduler, or the synchronous call's return) minus the
+    scheduled arrival, host monotonic clock; throughput = nodes of the timed
+    requests / (last completion - first timed arrival)."""
+    W, N = a.serve_warmup, a.serve_requests
+    R = W + N
+    P = min(a.serve_pools, R)
+    _, lens, kbs = I.config5_requests(P, I.SEED_BASE + 5)
     gen = torch.Generator(device="cuda").manual_seed(I.SEED_BASE + 5)
-    reqs = []
-    for i in range(R):
-        n, kb = int(lens[i]), int(kbs[i])
+    pools = []
+    for p in range(P):
+        n, kb = int(lens[p]), int(kbs[p])
         nxt, root = I.device_random_list(n, gen)
         key = I.device_keys(n, kb, gen)
-        reqs.append([nxt, nxt.clone(), key, root, n, kb, pbit.make_pool(nxt, key)])
+        pools.append({"next": nxt, "next0": nxt.clone(), "key": key, "root": root, "n": n, "kb": kb,
+                      "pool": pbit.make_pool(nxt, key), "ready": None})
     torch.cuda.synchronize()
-
-    def summarize(lat_ns, t_first, t_last, count_from):
-        lat = np.array(lat_ns[count_from:], dtype=np.float64) / 1e6
-        nodes = int(sum(int(lens[i]) for i in range(count_from, R)))
-        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "mean_ms": float(lat.mean()), "value": nodes / ((t_last - t_first) / 1e9), "unit": UNIT}
-
-    srv = pbit.Server(mem_budget_bytes=16 << 30, streams=4, max_batch=64)
-    clk = Clocks(local)
-    tickets = []
-    t0 = time.monotonic_ns() + 20_000_000
-    sched = [t0 + int(x * 1e9) for x in arr]
-    for i, r in enumerate(reqs):
-        while time.monotonic_ns() < sched[i]:
-            pass
-        tickets.append(srv.submit(r[6], r[3], r[4], 8 * r[5], 4))
-    done = []
-    for i, t in enumerate(tickets):
-        st, _ = srv.wait(t, 600000)
-        if st != pbit.OK:
-            raise pbit.PbitError(st, "served request")
-        done.append(srv.times(t)[1])
-    stats = srv.stats()
-    clocks = clk.stop()
-    srv.close()
-    W = a.serve_warmup
-    lat = [done[i] - sched[i] for i in range(R)]
-    served = summarize(lat, sched[W], max(done[W:]), W)
-
-    # the same trace served FIFO by the plain per-list call
-    for r in reqs:
-        r[0].copy_(r[1])
-    ws = pbit.alloc_workspace(max(pbit.workspace_size(1 << 24, 1, kb) for kb in (2, 4, 8)))
+    side = torch.cuda.Stream()
+    tune = {"digit_bits": 8}
+    ws = pbit.alloc_workspace(max(pbit.workspace_size(1 << 24, 1, kb, tune) for kb in (2, 4, 8)))
     stream = torch.cuda.current_stream()
-    torch.cuda.synchronize()
-    t0 = time.monotonic_ns() + 20_000_000
-    sched = [t0 + int(x * 1e9) for x in arr]
-    fdone = []
-    for i, r in enumerate(reqs):
-        while time.monotonic_ns() < sched[i]:
-            pass
-        st, _ = pbit.sort_pool_list(r[6], r[3], r[4], 8 * r[5], 4, ws=ws, stream=stream, check=False)
-        if st != pbit.OK:
-            raise pbit.PbitError(st, "FIFO request")
-        fdone.append(time.monotonic_ns())
-    flat = [fdone[i] - sched[i] for i in range(R)]
-    fifo = summarize(flat, sched[W], max(fdone[W:]), W)
-    offered = float(lens[W:].sum() / (arr[-1] - arr[W]))
-    return {"workload": "open-loop Poisson arrivals, mean gap 0.5 ms; lengths log-uniform in [2^4, 2^24]; "
-                        "uint16/uint32/uint64 keys 1:2:1, M = 8 x width; random order; uniform keys; "
-                        "16 GB admission budget, 4 streams, batches of up to 64",
-            "requests": a.serve_requests, "warmup_requests": W, "offered_nodes_per_s": offered,
-            "served": {**served, "batches": stats["batches"], "max_batch": stats["max_batch"],
-                       "peak_admitted_bytes": stats["peak_bytes"], "clocks": clocks},
-            "fifo_per_list": fifo,
-            "latency": "completion seen by the scheduler (served) or after the synchronous call returns "
-                       "(FIFO) minus the scheduled arrival, host monotonic clock"}
+
+    def restore(p):
+        pl = pools[p]
+        ev = torch.cuda.Event()
+        with torch.cuda.stream(side):
+            pl["next"].copy_(pl["next0"])
+            ev.record(side)
+        pl["ready"] = ev
+
+    def summarize(lat_ns, t_first, t_last, req_lens):
+        lat = np.array(lat_ns, dtype=np.float64) / 1e6
+        return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "value": float(sum(req_lens)) / ((t_last - t_first) / 1e9),
+                "unit": UNIT}
+
+    def served_arm(sched):
+        srv = pbit.Server(mem_budget_bytes=16 << 30, streams=4, max_batch=64, tune=tune)
+        tickets, done = [None] * R, [0] * R
+        oldest = 0  # first request whose completion has not been seen
+        next_poll = 0
+        for i in range(R):
+            p = i % P
+            if i >= P and done[i - P] == 0:  # the ring came round before the pool's request finished
+                st, _ = srv.wait(tickets[i - P], 600000)
+                if st != pbit.OK:
+                    raise pbit.PbitError(st, "served request")
+                done[i - P] = srv.times(tickets[i - P])[1]
+                restore(p)
+            while True:  # until the arrival time: note completions and restore their pools
+                while oldest < i and done[oldest]:
+                    oldest += 1
+                now = time.monotonic_ns()
+                if oldest < i and now >= next_poll:  # (polls spaced out: the server's lock is shared)
+                    next_poll = now + 20_000
+                    st, _ = srv.poll(tickets[oldest])
+                    if st != pbit.EPENDING:
+                        if st != pbit.OK:
+                            raise pbit.PbitError(st, "served request")
+                        done[oldest] = srv.times(tickets[oldest])[1]
+                        restore(oldest % P)
+                        next_poll = 0
+                        continue
+                if now >= sched[i]:
+                    break
+            pl = pools[p]
+            if pl["ready"] is not None:
+                pl["ready"].synchronize()
+                pl["ready"] = None
+            tickets[i] = srv.submit(pl["pool"], pl["root"], pl["n"], 8 * pl["kb"], 4)
+        for i in range(R):
+            if done[i] == 0:
+                st, _ = srv.wait(tickets[i], 600000)
+                if st != pbit.OK:
+                    raise pbit.PbitError(st, "served request")
+                done[i] = srv.times(tickets[i])[1]
+        stats = srv.stats()
+        srv.close()
+        return done, stats
+
+    def fifo_arm(sched):
+        done = [0] * R
+        for i in range(R):
+            p = i % P
+            pl = pools[p]
+            if pl["ready"] is not None:
+                pl["ready"].synchronize()
+                pl["ready"] = None
+            while time.monotonic_ns() < sched[i]:
+                pass
+            st, _ = pbit.sort_pool_list(pl["pool"], pl["root"], pl["n"], 8 * pl["kb"], 4, ws=ws, tune=tune,
+                                        stream=stream, check=False)
+            if st != pbit.OK:
+                raise pbit.PbitError(st, "FIFO request")
+            done[i] = time.monotonic_ns()
+            restore(p)
+        return done
+
+    out = {"workload": "open-loop Poisson arrivals; lengths log-uniform in [2^4, 2^24]; uint16/uint32/uint64 "
+                       "keys 1:2:1, M = 8 x width, K = 4 (GPU digit width 8 by tune in both arms); random order; "
+                       "uniform keys; 16 GB admission budget, 4 streams, batches of up to 64",
+           "requests": N, "warmup_requests": W, "pools": P,
+           "latency": "completion seen by the scheduler (served) or after the synchronous call returns (FIFO) "
+                      "minus the scheduled arrival, host monotonic clock",
+           "throughput": "nodes of the timed requests / (last completion - first timed arrival)"}
+    for name, gap in (("rate_2000_per_s", 0.5e-3), ("saturating_10000_per_s", 0.1e-3)):
+        arr = np.cumsum(I.rng(I.SEED_BASE + 50 + int(gap * 1e5)).exponential(gap, R))
+        req_lens = [int(lens[i % P]) for i in range(W, R)]
+        for pl in pools:
+            pl["next"].copy_(pl["next0"])
+            pl["ready"] = None
+        torch.cuda.synchronize()
+        clk = Clocks(local)
+        t0 = time.monotonic_ns() + 20_000_000
+        sched = [t0 + int(x * 1e9) for x in arr]
+        done, stats = served_arm(sched)
+        clocks = clk.stop()
+        served = summarize([done[i] - sched[i] for i in range(W, R)], sched[W], max(done[W:]), req_lens)
+        for pl in pools:
+            pl["next"].copy_(pl["next0"])
+            pl["ready"] = None
+        torch.cuda.synchronize()
+        t0 = time.monotonic_ns() + 20_000_000
+        sched = [t0 + int(x * 1e9) for x in arr]
+        fdone = fifo_arm(sched)
+        fifo = summarize([fdone[i] - sched[i] for i in range(W, R)], sched[W], max(fdone[W:]), req_lens)
+        out[name] = {"mean_gap_ms": gap * 1e3,
+                     "offered_nodes_per_s": float(sum(req_lens) / (arr[-1] - arr[W])),
+                     "served": {**served, "batches": stats["batches"], "max_batch": stats["max_batch"],
+                                "peak_workspace_bytes": stats["peak_bytes"], "clocks": clocks},
+                     "fifo_per_list": fifo,
+                     "served_over_fifo_throughput": served["value"] / fifo["value"]}
+    return out
 
 
 K_SWEEP = (1, 2, 4, 8, 16)

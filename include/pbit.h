@@ -296,21 +296,28 @@ pbit_status pbit_autotune_batched(const pbit_pool *pool, int32_t num_lists, cons
                                   size_t ws_bytes, int32_t reps, void *stream, pbit_tune *best, float *best_ms);
 
 /* ------------------------------------------------------------------ serving
- * A server owns a device arena of at most mem_budget_bytes on `device` and a
- * scheduler thread.  Requests are admitted while the workspace bytes of all
- * admitted requests fit in the budget; admitted requests are batched as they
- * arrive (continuous batching: requests that arrive while others run on the
- * GPU are admitted as memory frees up and run concurrently on up to
- * `streams` CUDA streams).  The caller owns each request's pool (device
+ * A server owns a device arena of mem_budget_bytes on `device` and a
+ * scheduler thread.  Requests queue in arrival order; the scheduler forms a
+ * batch from the head of the queue plus compatible queued requests (same key
+ * type, flags, M and K) and launches it as soon as one of its `streams` CUDA
+ * streams is free and the batch's workspace fits in the free part of the
+ * arena (first fit; the workspace returns to the arena when the batch
+ * completes).  So the workspaces of the batches in flight never exceed the
+ * budget, requests that arrive while others run on the GPU are admitted as
+ * streams and memory free up (continuous batching), and a large request
+ * waits only until enough memory is free (no later request overtakes the
+ * head of the queue).  `tune` (NULL = defaults; copied) applies to every
+ * batch, e.g. its digit width.  The caller owns each request's pool (device
  * memory) and keeps it alive until poll returns something other than
  * PBIT_EPENDING.
  */
 typedef struct pbit_server pbit_server;
 
 pbit_status pbit_serve_create(pbit_server **out, size_t mem_budget_bytes, int32_t device,
-                              int32_t streams, int32_t max_batch);
-/* Queue one request; *ticket identifies it.  PBIT_EAGAIN if the request can
- * never fit the budget; PBIT_EINVAL on bad arguments. */
+                              int32_t streams, int32_t max_batch, const pbit_tune *tune);
+/* Queue one request; *ticket identifies it.  PBIT_EAGAIN if the request's
+ * workspace alone exceeds the budget (it could never run); PBIT_EINVAL on bad
+ * arguments. */
 pbit_status pbit_serve_submit(pbit_server *s, const pbit_pool *pool, int32_t root, int64_t n,
                               int32_t M, int32_t K, uint64_t *ticket);
 /* PBIT_EPENDING while queued or running; otherwise the request's final status,
@@ -327,7 +334,7 @@ pbit_status pbit_serve_times(pbit_server *s, uint64_t ticket, int64_t *submit_ns
  * PBIT_EINVAL).  PBIT_EPENDING if it has not finished. */
 pbit_status pbit_serve_release(pbit_server *s, uint64_t ticket);
 /* Server counters: [0] submitted, [1] completed, [2] batches launched,
- * [3] max requests in one batch, [4] peak admitted bytes. */
+ * [3] max requests in one batch, [4] peak workspace bytes in flight. */
 void pbit_serve_stats(pbit_server *s, int64_t *out5);
 void pbit_serve_destroy(pbit_server *s);
 

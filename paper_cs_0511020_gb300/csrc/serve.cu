@@ -1,18 +1,24 @@
 // serve.cu -- request server: continuous batching of sort requests.
 //
 // Callers submit lists that live in their own device pools.  A scheduler
-// thread admits queued requests into batches that fit a slot of the device
-// arena (the memory budget split over the server's CUDA streams), so a batch
-// formed from requests that arrived while other batches run on the GPU is
-// launched as soon as a slot frees up, and up to `streams` batches overlap on
-// the device.  A batch is one sort call whose lists are its requests (each
-// list with its own pool, relinked in place); requests of one batch share
-// key type, flags and M.  If a batch fails (a malformed list), its requests
-// are retried one by one so each gets its own status.
+// thread forms batches from the queue and launches each one as soon as a
+// CUDA stream is free and its workspace fits in the free part of the device
+// arena (the memory budget): the arena is carved per batch, first fit, and
+// given back when the batch completes, so the sum of the workspaces in
+// flight never exceeds the budget, and a large request waits only until
+// enough memory has been freed (batches are formed from the head of the
+// queue, in arrival order, so no request waits behind later ones).
+// Requests that arrive while other batches run on the GPU join the next
+// batch; up to `streams` batches overlap on the device.  A batch is one sort
+// call whose lists are its requests (each list with its own pool, relinked in
+// place); requests of one batch share key type, flags, M and K.  If a batch
+// fails (a malformed list), its requests are retried one by one so each gets
+// its own status.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -39,14 +45,14 @@ static int64_t now_ns() {
         .count();
 }
 
+// One CUDA stream and what a batch in flight on it holds.
 struct SrvSlot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
-    unsigned char *ws = nullptr;
-    size_t ws_bytes = 0;
     ListDesc *h_desc = nullptr;  // pinned, max_batch entries
     int32_t *h_out = nullptr;    // pinned: status, then one head per list
     std::vector<SrvReq *> reqs;
+    size_t ws_off = 0, ws_bytes = 0;  // its workspace in the arena
     bool busy = false;
 };
 
@@ -55,12 +61,50 @@ static bool compatible(const SrvReq *a, const SrvReq *b) {
            !a->solo && !b->solo;
 }
 
-static size_t batch_ws(int64_t nodes, int32_t lists, int kb) {
-    size_t w = 0;
-    if (pbit_workspace_size(nodes, lists, kb, nullptr, &w) != PBIT_OK)
-        return (size_t)-1;
-    return w;
-}
+// First-fit allocator over the arena's byte range (256-byte granules).
+struct ArenaMap {
+    std::map<size_t, size_t> free_;  // offset -> length, coalesced
+    void init(size_t bytes) {
+        free_.clear();
+        if (bytes)
+            free_[0] = bytes;
+    }
+    size_t largest() const {
+        size_t m = 0;
+        for (const auto &kv : free_)
+            m = std::max(m, kv.second);
+        return m;
+    }
+    bool take(size_t bytes, size_t *off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < bytes)
+                continue;
+            *off = it->first;
+            const size_t rest = it->second - bytes;
+            const size_t at = it->first + bytes;
+            free_.erase(it);
+            if (rest)
+                free_[at] = rest;
+            return true;
+        }
+        return false;
+    }
+    void give(size_t off, size_t bytes) {
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {  // merge with the next range
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {  // and with the previous one
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
 
 }  // namespace pbit
 
@@ -70,6 +114,10 @@ struct pbit_server {
     int device = 0;
     int max_batch = 64;
     unsigned char *arena = nullptr;
+    size_t arena_bytes = 0;
+    ArenaMap amap;
+    bool has_tune = false;
+    pbit_tune tune{};
     std::vector<SrvSlot> slots;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -83,24 +131,38 @@ struct pbit_server {
 
 namespace pbit {
 
-// Take a batch for a slot from the queue (lock held).
-static std::vector<SrvReq *> take_batch(pbit_server *s, const SrvSlot &slot, int64_t *nodes_out) {
+// Workspace bytes of a batch of `lists` lists with `nodes` nodes in all.
+static size_t batch_ws(const pbit_server *s, int64_t nodes, int32_t lists, const SrvReq *r) {
+    Tune t;
+    if (!resolve_tune(s->has_tune ? &s->tune : nullptr, nodes, r->pool.key_type, r->K, &t))
+        return (size_t)-1;
+    return bind(compute_sizes(nodes, lists, r->pool.key_type, t, device_sms()), nullptr, nullptr, nullptr);
+}
+
+// Take a batch from the head of the queue whose workspace fits the largest
+// free range of the arena (lock held).  Returns an empty batch when the
+// head does not fit yet: it waits for memory, and nothing overtakes it.
+static std::vector<SrvReq *> take_batch(pbit_server *s, int64_t *nodes_out, size_t *ws_out) {
     std::vector<SrvReq *> b;
     if (s->queue.empty())
         return b;
+    const size_t room = s->amap.largest();
     SrvReq *first = s->queue.front();
     int64_t nodes = first->n;
-    if (batch_ws(nodes, 1, first->pool.key_type) > slot.ws_bytes)
-        return b;  // waits for a slot that is large enough (all slots are equal: never)
+    size_t need = batch_ws(s, nodes, 1, first);
+    if (need > room)
+        return b;
     b.push_back(first);
     s->queue.pop_front();
     if (!first->solo) {
         const size_t window = 256;  // how far down the queue to look for companions
         for (size_t i = 0; i < s->queue.size() && i < window && (int)b.size() < s->max_batch;) {
             SrvReq *r = s->queue[i];
-            if (compatible(first, r) && batch_ws(nodes + r->n, (int32_t)b.size() + 1, r->pool.key_type) <= slot.ws_bytes) {
+            size_t w = 0;
+            if (compatible(first, r) && (w = batch_ws(s, nodes + r->n, (int32_t)b.size() + 1, r)) <= room) {
                 b.push_back(r);
                 nodes += r->n;
+                need = w;
                 s->queue.erase(s->queue.begin() + (ptrdiff_t)i);
             } else {
                 ++i;
@@ -108,10 +170,11 @@ static std::vector<SrvReq *> take_batch(pbit_server *s, const SrvSlot &slot, int
         }
     }
     *nodes_out = nodes;
+    *ws_out = (need + 255) & ~(size_t)255;
     return b;
 }
 
-static pbit_status launch_batch(SrvSlot &slot, const std::vector<SrvReq *> &b, int64_t nodes) {
+static pbit_status launch_batch(pbit_server *s, SrvSlot &slot, const std::vector<SrvReq *> &b, int64_t nodes) {
     const SrvReq *r0 = b[0];
     const int L = (int)b.size();
     int32_t ob = 0;
@@ -125,12 +188,13 @@ static pbit_status launch_batch(SrvSlot &slot, const std::vector<SrvReq *> &b, i
         slot.h_desc[i] = d;
     }
     Tune t;
-    resolve_tune(nullptr, nodes, r0->pool.key_type, r0->K, &t);
+    if (!resolve_tune(s->has_tune ? &s->tune : nullptr, nodes, r0->pool.key_type, r0->K, &t))
+        return PBIT_EINVAL;
     const int sms = device_sms();
     Sizes z = compute_sizes(nodes, L, r0->pool.key_type, t, sms);
     Ctx c;
     MemsetList ms;
-    if (bind(z, slot.ws, &c, &ms) > slot.ws_bytes)
+    if (bind(z, s->arena + slot.ws_off, &c, &ms) > slot.ws_bytes)
         return PBIT_ENOMEM;
     c.flags = r0->pool.flags;
     c.shared_pool = 0;
@@ -178,6 +242,8 @@ static void serve_loop(pbit_server *s) {
                 }
             }
             s->in_flight_bytes -= (int64_t)slot.ws_bytes;
+            s->amap.give(slot.ws_off, slot.ws_bytes);
+            slot.ws_bytes = 0;
             slot.reqs.clear();
             slot.busy = false;
             progress = true;
@@ -188,15 +254,26 @@ static void serve_loop(pbit_server *s) {
             if (slot.busy || s->queue.empty())
                 continue;
             int64_t nodes = 0;
-            std::vector<SrvReq *> b = take_batch(s, slot, &nodes);
+            size_t need = 0;
+            std::vector<SrvReq *> b = take_batch(s, &nodes, &need);
             if (b.empty())
+                break;  // the head waits for memory
+            size_t off = 0;
+            if (!s->amap.take(need, &off)) {  // (take_batch checked the room: cannot happen)
+                for (size_t i = b.size(); i-- > 0;)
+                    s->queue.push_front(b[i]);
                 break;
+            }
+            slot.ws_off = off;
+            slot.ws_bytes = need;
             slot.busy = true;  // owned by this thread while the lock is released
             lk.unlock();       // launching takes a while: let submitters in
-            const pbit_status rc = launch_batch(slot, b, nodes);
+            const pbit_status rc = launch_batch(s, slot, b, nodes);
             lk.lock();
             slot.busy = false;
             if (rc != PBIT_OK) {
+                s->amap.give(slot.ws_off, slot.ws_bytes);
+                slot.ws_bytes = 0;
                 for (SrvReq *r : b) {
                     r->status = rc;
                     r->done_ns = now_ns();
@@ -228,24 +305,30 @@ static void serve_loop(pbit_server *s) {
 extern "C" {
 
 pbit_status pbit_serve_create(pbit_server **out, size_t mem_budget_bytes, int32_t device, int32_t streams,
-                              int32_t max_batch) {
+                              int32_t max_batch, const pbit_tune *tune) {
     if (!out || streams < 1 || streams > 16 || max_batch < 1 || mem_budget_bytes < (1u << 20))
+        return PBIT_EINVAL;
+    Tune probe;
+    if (tune && !resolve_tune(tune, 1 << 20, 4, 4, &probe))
         return PBIT_EINVAL;
     if (cudaSetDevice(device) != cudaSuccess)
         return PBIT_ECUDA;
     pbit_server *s = new pbit_server();
     s->device = device;
     s->max_batch = max_batch;
-    const size_t per = (mem_budget_bytes / (size_t)streams) & ~(size_t)255;
-    if (cudaMalloc((void **)&s->arena, per * (size_t)streams) != cudaSuccess) {
+    if (tune) {
+        s->has_tune = true;
+        s->tune = *tune;
+    }
+    s->arena_bytes = mem_budget_bytes & ~(size_t)255;
+    if (cudaMalloc((void **)&s->arena, s->arena_bytes) != cudaSuccess) {
         delete s;
         return PBIT_ENOMEM;
     }
+    s->amap.init(s->arena_bytes);
     s->slots.resize((size_t)streams);
     for (int i = 0; i < streams; ++i) {
         SrvSlot &sl = s->slots[(size_t)i];
-        sl.ws = s->arena + per * (size_t)i;
-        sl.ws_bytes = per;
         if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost((void **)&sl.h_desc, sizeof(ListDesc) * (size_t)max_batch) != cudaSuccess ||
@@ -267,8 +350,6 @@ pbit_status pbit_serve_submit(pbit_server *s, const pbit_pool *pool, int32_t roo
         return PBIT_EBADLIST;
     if (n == 0 && root != -1)
         return PBIT_EBADLIST;
-    if (n > 0 && batch_ws(n, 1, pool->key_type) > s->slots[0].ws_bytes)
-        return PBIT_EAGAIN;  // can never fit the budget
     SrvReq *r = new SrvReq();
     r->pool = *pool;
     r->root = root;
@@ -276,6 +357,10 @@ pbit_status pbit_serve_submit(pbit_server *s, const pbit_pool *pool, int32_t roo
     r->M = M;
     r->K = K;
     r->submit_ns = now_ns();
+    if (n > 0 && batch_ws(s, n, 1, r) > s->arena_bytes) {
+        delete r;
+        return PBIT_EAGAIN;  // can never fit the budget
+    }
     {
         std::lock_guard<std::mutex> g(s->mu);
         r->ticket = s->next_ticket++;

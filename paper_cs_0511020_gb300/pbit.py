@@ -84,7 +84,7 @@ def lib():
         L.pbit_profile_read.restype = i32
         L.pbit_profile_read.argtypes = [vp, i32]
         L.pbit_serve_create.restype = ctypes.c_int
-        L.pbit_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, i32, i32, i32]
+        L.pbit_serve_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, i32, i32, i32, vp]
         L.pbit_serve_submit.restype = ctypes.c_int
         L.pbit_serve_submit.argtypes = [vp, vp, i32, i64, i32, i32, ctypes.POINTER(ctypes.c_uint64)]
         L.pbit_serve_poll.restype = ctypes.c_int
@@ -417,10 +417,11 @@ class Server:
     whose pools the caller keeps alive until they finish."""
 
     def __init__(self, mem_budget_bytes: int = 16 << 30, device: int = 0, streams: int = 4,
-                 max_batch: int = 64):
+                 max_batch: int = 64, tune=None):
         self._h = ctypes.c_void_p()
+        tune, tp = _tune_ptr(tune)
         st = lib().pbit_serve_create(ctypes.byref(self._h), int(mem_budget_bytes), int(device), int(streams),
-                                     int(max_batch))
+                                     int(max_batch), tp)
         if st != OK:
             raise PbitError(st, "pbit_serve_create")
         self._keep = {}

@@ -129,3 +129,85 @@ def test_serve_times_and_release(pb):
             assert srv.release(t) == pb.EINVAL
     finally:
         srv.close()
+
+
+def _submit_many(pb, srv, specs, seed):
+    """Submit lists of the given (n, key bytes) back to back; returns the
+    requests with their inputs for checking."""
+    reqs = []
+    for i, (n, kb) in enumerate(specs):
+        nxt, root = I.random_list(n, seed + i)
+        key = I.uniform_keys(n, kb, seed + 1000 + i)
+        d_next, d_key = torch.from_numpy(nxt.copy()).cuda(), _dev(key)
+        reqs.append((nxt, key, root, d_next, d_key, kb))
+    torch.cuda.synchronize()
+    out = []
+    for nxt, key, root, d_next, d_key, kb in reqs:
+        t = srv.submit(pb.make_pool(d_next, d_key), root, nxt.size, 8 * kb, 4, keep=(d_next, d_key))
+        out.append((t, nxt, key, root, d_next, kb))
+    return out
+
+
+def _check_all(pb, srv, reqs, alone=True):
+    for t, nxt, key, root, d_next, kb in reqs:
+        st, r = srv.wait(t, 300000)
+        assert st == pb.OK, pb.status_string(st)
+        got = d_next.cpu().numpy()
+        want, wr, _ = O.pbit_sort(nxt, key, root, 8 * kb, 4)
+        assert r == wr and (got == want).all()
+        if alone:
+            a, ra = _alone(pb, nxt, key, root, 8 * kb)
+            assert ra == r and (a == got).all()
+
+
+def test_serve_merges_requests_that_arrive_while_the_gpu_is_busy(pb):
+    """Continuous batching: while a large request occupies the only stream,
+    the short requests that arrive queue up and are launched together, as
+    batches of several requests; every result equals the oracle's and the
+    same list sorted alone."""
+    srv = pb.Server(mem_budget_bytes=4 << 30, streams=1, max_batch=32)
+    try:
+        g = I.rng(1301)
+        specs = [(1 << 22, 4)] + [(int(g.integers(2000, 40000)), 4) for _ in range(120)]
+        reqs = _submit_many(pb, srv, specs, 1400)
+        _check_all(pb, srv, reqs[:1] + reqs[1::10])
+        _check_all(pb, srv, reqs, alone=False)
+        stats = srv.stats()
+        assert stats["completed"] == len(reqs)
+        assert stats["batches"] < len(reqs), stats
+        assert stats["max_batch"] > 1, stats
+    finally:
+        srv.close()
+
+
+def test_serve_admits_large_requests_as_memory_frees(pb):
+    """Admission by the budget: three requests whose workspaces each take
+    most of the arena run one after another (never two at once), with short
+    requests around them; all finish and the workspace in flight never
+    exceeds the budget."""
+    n_big = 1 << 21
+    ws_big = pb.workspace_size(n_big, 1, 4)
+    budget = (ws_big * 3) // 2
+    srv = pb.Server(mem_budget_bytes=budget, streams=3, max_batch=8)
+    try:
+        specs = [(n_big, 4), (3000, 4), (n_big, 4), (9000, 8), (n_big, 4), (700, 2)]
+        reqs = _submit_many(pb, srv, specs, 1500)
+        _check_all(pb, srv, reqs, alone=False)
+        stats = srv.stats()
+        assert stats["completed"] == len(reqs)
+        assert 0 < stats["peak_bytes"] <= budget
+    finally:
+        srv.close()
+
+
+def test_serve_with_a_tune(pb):
+    """A server-wide tune (8-bit GPU digits) gives the same results."""
+    srv = pb.Server(mem_budget_bytes=2 << 30, streams=2, max_batch=16, tune={"digit_bits": 8})
+    try:
+        g = I.rng(1601)
+        specs = [(int(np.clip(np.floor(2.0 ** (4 + 16 * g.random())), 16, 1 << 20)), int(g.choice([2, 4, 8])))
+                 for _ in range(30)]
+        reqs = _submit_many(pb, srv, specs, 1700)
+        _check_all(pb, srv, reqs, alone=False)
+    finally:
+        srv.close()
