@@ -42,24 +42,29 @@ def parse():
     ap.add_argument("--log2n", type=int, default=27, help="list size (27 = the benchmark workload)")
     ap.add_argument("--key-bits", type=int, default=32,
                     help="keys uniform over this many low bits and M = this (32 = the benchmark workload)")
-    ap.add_argument("--digit-bits", type=int, default=0,
-                    help="GPU digit width of the timed sort (0 = the call's K)")
+    ap.add_argument("--digit-bits", type=int, default=8,
+                    help="GPU digit width of the timed sort (tune; 0 = the call's K, 4)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-log2n", type=int, default=24)
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-list batched leg")
     ap.add_argument("--no-serve", action="store_true", help="skip the request-serving leg")
     ap.add_argument("--batched-lists", type=int, default=4096)
+    ap.add_argument("--cpu-batched-lists", type=int, default=512,
+                    help="lists of the batched workload in the all-cores oracle sample")
     ap.add_argument("--serve-requests", type=int, default=20000, help="timed requests of each serving trace")
     ap.add_argument("--serve-warmup", type=int, default=1000)
     ap.add_argument("--serve-pools", type=int, default=1000, help="device pools the request stream cycles through")
     return ap.parse_args()
 
 
-def workload(log2n, key_bits=32):
+def workload(log2n, key_bits=32, digit_bits=0):
     return {"workload": f"pbit_sort_list: one 2^{log2n}-node list, SoA int32 next + uint32 key, "
                         f"seeded random list order, uniform keys, M={key_bits}, K=4"
                         + ("" if key_bits == 32 else f" (keys below 2^{key_bits})"),
             "n": 1 << log2n, "key": "uint32", "layout": "SoA", "M": key_bits, "K": 4,
+            "gpu_digit_bits": digit_bits or 4,
+            "digit_bits_note": "the GPU's MSD passes split on this many bits (tune); the result is the same for "
+                               "any width, K=4 fixes only the paper's digit",
             "l2": "inputs (1 GiB at 2^27) larger than L2; no flush"}
 
 
@@ -181,7 +186,7 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot / a.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": workload(a.log2n, a.key_bits),
+        "config": workload(a.log2n, a.key_bits, a.digit_bits),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
@@ -347,7 +352,7 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32", "data": "synthetic",
-        "config": dict(workload(a.log2n, a.key_bits), parallelism=("replicas" if world > 1 else "single GPU"),
+        "config": dict(workload(a.log2n, a.key_bits, a.digit_bits), parallelism=("replicas" if world > 1 else "single GPU"),
                        timing="device time per step from two CUDA events on the launching stream around the "
                               "sort call; next[] restored from a device copy before each step, outside the "
                               "events; per-kernel figures from a second, profiled run of the same steps"),
@@ -372,9 +377,12 @@ def run_ours(a):
 
 def run_batched(a, torch, pbit, I, local=0):
     """Batched workload: 4096 lists in one pool, lengths log-uniform in
-    [16, 2^20], uint32 keys, random order per list, M=32.  The batch is
-    autotuned, captured once as a CUDA graph and replayed; the same lists are
-    then sorted one pbit_sort_list call at a time (the plain per-list path)."""
+    [16, 2^20], uint32 keys, random order per list, M=32, K=4.  The batch is
+    autotuned (digit width x shared-memory cutoff x ruler stride), captured
+    once as a CUDA graph and replayed; the same lists are then sorted one
+    pbit_sort_list call at a time (the plain per-list path, with the same
+    tune).  Both paths are timed on both clocks: CUDA events on the stream
+    around the whole step, and the host wall clock around launch + result."""
     gen = torch.Generator(device="cuda").manual_seed(I.SEED_BASE + 4)
     lens = I.config4_lengths(I.SEED_BASE + 4, a.batched_lists)
     d_next0, d_key, d_roots, d_off = I.device_batched_pool(lens, 4, gen)
@@ -382,7 +390,7 @@ def run_batched(a, torch, pbit, I, local=0):
     d_next = d_next0.clone()
     pool = pbit.make_pool(d_next, d_key)
     best, tune_ms = pbit.autotune_batched(pool, d_roots, d_off, 32, 4, reps=2)
-    g = pbit.Graph.batched(pool, d_roots, d_off, 32, 4)
+    g = pbit.Graph.batched(pool, d_roots, d_off, 32, 4)  # tune = NULL: the autotuned choice
     stream = torch.cuda.current_stream()
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
@@ -391,15 +399,20 @@ def run_batched(a, torch, pbit, I, local=0):
         g.launch(stream)
         g.result(stream)
     clk = Clocks(local)
+    graph_wall = []
     for i in range(a.steps):
         d_next.copy_(d_next0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         e0[i].record(stream)
         g.launch(stream)
         e1[i].record(stream)
-        g.result(stream)  # status of this replay (synchronizes)
+        g.result(stream)  # status of this replay (synchronizes; raises on an error)
+        graph_wall.append(time.perf_counter() - t0)
     clocks = clk.stop()
     graph_ms = [e0[i].elapsed_time(e1[i]) for i in range(a.steps)]
     gm = statistics.median(graph_ms)
+    gw = 1e3 * statistics.median(graph_wall)
 
     # the plain per-list path: one synchronous pbit_sort_list per list, in
     # order, each on its own slice of the pool with list-local indices
@@ -409,37 +422,76 @@ def run_batched(a, torch, pbit, I, local=0):
     loc0 = torch.where(d_next0 >= 0, d_next0 - base, d_next0)
     loc = loc0.clone()
     roots_loc = (d_roots - d_off[:-1].to(torch.int32)).cpu().numpy()
-    ws = pbit.alloc_workspace(pbit.workspace_size(int(lens.max()), 1, 4))
+    tune = {k: best[k] for k in ("digit_bits", "smem_cutoff", "ruler_stride")}
+    ws = pbit.alloc_workspace(pbit.workspace_size(int(lens.max()), 1, 4, tune))
     pools = [pbit.Pool(loc.data_ptr() + 4 * int(off[i]), 4, d_key.data_ptr() + 4 * int(off[i]), 4, 4, 0,
                        int(lens[i]), 0, 0) for i in range(lens.size)]
-    fifo_s = []
+    fifo_wall, fifo_ev = [], []
     for rep in range(2):
         loc.copy_(loc0)
         torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        f0.record(stream)
         for i in range(lens.size):
-            st, _ = pbit.sort_pool_list(pools[i], int(roots_loc[i]), int(lens[i]), 32, 4, ws=ws, stream=stream,
-                                        check=False)
+            st, _ = pbit.sort_pool_list(pools[i], int(roots_loc[i]), int(lens[i]), 32, 4, ws=ws, tune=tune,
+                                        stream=stream, check=False)
             if st != pbit.OK:
                 raise pbit.PbitError(st, "per-list sort")
+        f1.record(stream)
         torch.cuda.synchronize()
-        fifo_s.append(time.perf_counter() - t0)
+        fifo_wall.append(1e3 * (time.perf_counter() - t0))
+        fifo_ev.append(f0.elapsed_time(f1))
     # both paths give the same next[] (list-local vs pool indices)
     same = bool(torch.equal(torch.where(loc >= 0, loc + base, loc), d_next))
-    fm = min(fifo_s)
+    fw, fe = min(fifo_wall), min(fifo_ev)
     out = {"workload": f"{lens.size} lists in one SoA pool, lengths log-uniform in [16, 2^20] (seeded), "
                        "uint32 keys uniform, random order per list, M=32, K=4",
            "nodes": total, "lists": int(lens.size),
-           "graph": {"value": total / (gm / 1e3), "unit": UNIT, "ms_per_step": gm, "steps": a.steps,
-                     "graph_nodes": g.node_count(),
-                     "timing": "CUDA events around each graph replay; next[] restored before, outside them"},
-           "per_list": {"value": total / fm, "unit": UNIT, "ms": 1e3 * fm,
-                        "timing": "host wall clock over the whole loop of synchronous pbit_sort_list calls, "
-                                  "best of 2"},
-           "speedup_vs_per_list": fm * 1e3 / gm, "same_result": same, "clocks": clocks,
-           "autotuned": {**best, "median_ms": tune_ms}}
+           "graph": {"value": total / (gm / 1e3), "unit": UNIT, "ms_per_step": gm, "wall_ms_per_step": gw,
+                     "steps": a.steps, "graph_nodes": g.node_count(),
+                     "timing": "median over the steps; ms_per_step: CUDA events around each graph replay; "
+                               "wall_ms_per_step: host clock around launch + status read-back; next[] restored "
+                               "before, outside both"},
+           "per_list": {"value": total / (fe / 1e3), "unit": UNIT, "ms": fe, "wall_ms": fw,
+                        "timing": "best of 2 loops over all lists; ms: CUDA events before the first and after the "
+                                  "last call; wall_ms: host clock over the loop of synchronous calls"},
+           "speedup_vs_per_list": {"events": fe / gm, "wall": fw / gw},
+           "same_result": same, "clocks": clocks,
+           "autotuned": {**best, "median_ms": tune_ms,
+                         "searched": {"digit_bits": [4, 8], "smem_cutoff": [128, 256, 512],
+                                      "ruler_stride": [16, 32, 64, 128]}}}
     g.close()
+    if not a.no_cpu_baseline:
+        out["cpu_baseline_all_cores"] = oracle_batched_sample(lens, a.cpu_batched_lists)
     return out
+
+
+def oracle_batched_sample(lens, count):
+    """The oracle on every host core at once: `count` lists of the batched
+    workload (evenly spaced through the 4096, so their lengths span the
+    range), one list per thread at a time (the C oracle runs outside the
+    Python lock), nodes / wall time."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from oracle import oracle as O
+    from paper_cs_0511020_gb300 import inputs as I
+    cores = len(os.sched_getaffinity(0))
+    pick = np.linspace(0, lens.size - 1, count).astype(np.int64)
+    lists = []
+    for j in pick:
+        n = int(lens[j])
+        nxt, root = I.random_list(n, I.SEED_BASE + 40000 + int(j))
+        lists.append((nxt, I.uniform_keys(n, 4, I.SEED_BASE + 50000 + int(j)), root))
+    O.lib()
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(lambda x: O.pbit_sort(x[0], x[1], x[2], 32, 4), lists))
+    dt = time.perf_counter() - t0
+    nodes = int(sum(int(lens[j]) for j in pick))
+    return {"value": nodes / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{count} of the {lens.size} lists (evenly spaced, {nodes} nodes), the oracle on "
+                      f"{cores} threads ({dt:.1f} s)"}
 
 
 def run_serve(a, torch, pbit, I, local=0):
