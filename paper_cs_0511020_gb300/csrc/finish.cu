@@ -336,8 +336,8 @@ __global__ void __launch_bounds__(32 * kFWarps) k_finish(Ctx c) {
 // and writes the node ids to F.  A window is a stable counting split: each
 // warp ranks its contiguous slice of the bucket group by group (32 elements:
 // the lanes holding the same digit are found with one ballot per digit bit,
-// the lowest of them adds the group's count to the warp's shared counter of
-// that digit and passes the old value on), one thread per digit then turns
+// each reads the warp's shared counter of that digit and the lowest of them
+// writes it back advanced by the group's count), one thread per digit then turns
 // the (warp, digit) counts into each warp's first slot (digit-major, warps in
 // slice order: stable), and every element moves to its slot in the other
 // buffer.  This replaces the further global passes, their planning and the
@@ -482,11 +482,15 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
                             diff |= __ballot_sync(kFull, mb != 0) ^ (unsigned)mb;
                         }
                         const unsigned peers = __ballot_sync(kFull, valid) & ~diff;
-                        const int leader = __ffs(peers) - 1;
-                        uint32_t before = 0;
-                        if (valid && lane == leader)
-                            before = atomicAdd(&S.wcnt[wid][dig], (uint32_t)__popc(peers));
-                        rnk[i] = __shfl_sync(kFull, before, leader & 31) + (uint32_t)__popc(peers & lt);
+                        // every lane reads its digit's count; the lowest peer
+                        // writes it back advanced (peers share one digit, other
+                        // lowest peers write other counters)
+                        const uint32_t before = S.wcnt[wid][dig];
+                        const unsigned below = peers & lt;
+                        if (valid && below == 0)
+                            S.wcnt[wid][dig] = before + (uint32_t)__popc(peers);
+                        __syncwarp();
+                        rnk[i] = before + (uint32_t)__popc(below);
                     }
                 }
                 __syncthreads();

@@ -468,11 +468,14 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
                 diff |= __ballot_sync(kFull, m != 0) ^ (unsigned)m;
             }
             const unsigned peers = __ballot_sync(kFull, valid) & ~diff;
-            const int leader = __ffs(peers) - 1;  // (an invalid lane's value is never used)
-            uint32_t before = 0;
-            if (valid && lane == leader)
-                before = atomicAdd(&wc[dig], (uint32_t)__popc(peers));
-            rnk[i] = __shfl_sync(kFull, before, leader & 31) + (uint32_t)__popc(peers & lt);
+            // every lane reads its digit's count; the lowest peer writes it
+            // back advanced (the lowest peers of one group hold distinct digits)
+            const uint32_t before = wc[dig];
+            const unsigned below = peers & lt;
+            if (valid && below == 0)
+                wc[dig] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            rnk[i] = before + (uint32_t)__popc(below);
         }
         __syncthreads();
         // the next tile's output bases: loads in flight during the rest of this tile
