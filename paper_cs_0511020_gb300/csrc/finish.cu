@@ -518,9 +518,13 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
                         if (pos < len) {
                             const KeyT k = ka[pos];
                             const uint32_t p = S.wcnt[wid][digit_of<KeyT>(k, wl, dmask)] + rnk[i];
-                            if (!last)
-                                kb[p] = k;
-                            ib[p] = ia[pos];
+                            if (p < (uint32_t)len) {
+                                if (!last)
+                                    kb[p] = k;
+                                ib[p] = ia[pos];
+                            } else {
+                                set_status(c.status, kStOverflow);  // (inconsistent counts: cannot happen)
+                            }
                         }
                     }
                 }
@@ -528,6 +532,7 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
 #pragma unroll
                 for (int x = 0; x < kMidWarps; ++x)  // counters of the next window
                     S.wcnt[x][tid] = 0;
+                __syncthreads();  // zeroed before any warp ranks the next window
                 res = ib;
                 KeyT *tk = ka;  // the other buffer is the next window's source
                 ka = kb;

@@ -507,8 +507,12 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
             const int pos = wid * (32 * k8Items) + i * 32 + lane;
             if (pos < cnt) {
                 const uint32_t lp = wc[digit_of<KeyT>(key[i], lo, dmask)] + rnk[i];
-                ok[lp] = key[i];
-                oi[lp] = idx[i];
+                if (lp < (uint32_t)cnt) {
+                    ok[lp] = key[i];
+                    oi[lp] = idx[i];
+                } else {
+                    set_status(c.status, kStOverflow);  // (inconsistent counts: cannot happen)
+                }
             }
         }
         __syncthreads();
