@@ -47,8 +47,8 @@ static_assert(k8Bins == k8TPB, "one thread per bucket in the per-tile steps");
 // CTAs; the keys of the next tile are copied into shared memory by the bulk
 // copy engine while the current one is counted.
 struct Hist8Smem {
-    uint32_t h[k8Warps][k8Bins];  // per-warp digit counts
-    unsigned long long s_and, s_or;
+    uint32_t h[2][k8Warps][k8Bins];  // per-warp digit counts, one set per stage
+    unsigned long long s_and[2], s_or[2];
     int32_t seg[2], cnt[2], shk[2], lo[2], hi[2];
     int32_t cs, ctb_next;         // the issuing thread's segment cursor
     alignas(8) uint64_t bar[2];
@@ -100,11 +100,13 @@ __global__ void __launch_bounds__(k8TPB) k_hist8(Ctx c, int it) {
         return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     using U = typename KeyWord<KeyT>::U;
-    for (int w = 0; w < k8Warps; ++w)
-        S.h[w][tid] = 0;
+    for (int w = 0; w < k8Warps; ++w) {
+        S.h[0][w][tid] = 0;
+        S.h[1][w][tid] = 0;
+    }
     if (tid == 0) {
-        S.s_and = ~0ull;
-        S.s_or = 0ull;
+        S.s_and[0] = S.s_and[1] = ~0ull;
+        S.s_or[0] = S.s_or[1] = 0ull;
         mbar_init(&S.bar[0], 1);
         mbar_init(&S.bar[1], 1);
         fence_mbar_init();
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(k8TPB) k_hist8(Ctx c, int it) {
                 const U kv = (U)sk[pos];
                 w_and &= kv;
                 w_or |= kv;
-                atomicAdd(&S.h[wid][(unsigned)(kv >> lo) & dmask], 1u);
+                atomicAdd(&S.h[st][wid][(unsigned)(kv >> lo) & dmask], 1u);
             }
         }
 #pragma unroll
@@ -152,27 +154,28 @@ __global__ void __launch_bounds__(k8TPB) k_hist8(Ctx c, int it) {
             w_or |= __shfl_xor_sync(kFull, w_or, o);
         }
         if (lane == 0) {  // keys are zero-extended to 64 bits
-            atomicAnd(&S.s_and, (unsigned long long)w_and);
-            atomicOr(&S.s_or, (unsigned long long)w_or);
+            atomicAnd(&S.s_and[st], (unsigned long long)w_and);
+            atomicOr(&S.s_or[st], (unsigned long long)w_or);
         }
         __syncthreads();
+        // (the next tile counts into the other set: the barrier at its copy
+        // wait orders these reads and clears before that set's next use)
         uint32_t sum = 0;
 #pragma unroll
         for (int w = 0; w < k8Warps; ++w) {
-            sum += S.h[w][tid];
-            S.h[w][tid] = 0;
+            sum += S.h[st][w][tid];
+            S.h[st][w][tid] = 0;
         }
         if ((int64_t)g < c.row_cap)
             c.tcnt[cur][(int64_t)g * k8Bins + tid] = sum;
         else
             set_status(c.status, kStOverflow);
         if (tid == 0) {  // this tile's AND/OR into its segment's
-            atomicAnd(&c.pand[cur][S.seg[st]], S.s_and);
-            atomicOr(&c.por[cur][S.seg[st]], S.s_or);
-            S.s_and = ~0ull;
-            S.s_or = 0ull;
+            atomicAnd(&c.pand[cur][S.seg[st]], S.s_and[st]);
+            atomicOr(&c.por[cur][S.seg[st]], S.s_or[st]);
+            S.s_and[st] = ~0ull;
+            S.s_or[st] = 0ull;
         }
-        __syncthreads();  // counters cleared, AND/OR reset, stage free for the copy after next
         st ^= 1;
     }
     if (tid == 0 && my_elems)
@@ -180,27 +183,57 @@ __global__ void __launch_bounds__(k8TPB) k_hist8(Ctx c, int it) {
 }
 
 // ------------------------------------------------------------- tile_scan8
-// Per chunk of kScanChunk tiles of an active segment, one thread per digit:
-// each tile's counts become the exclusive prefix within the chunk, and the
-// chunk totals go to ctot.
-__global__ void __launch_bounds__(k8TPB) k_tile_scan8(Ctx c, int it) {
+// Per chunk of kScanChunk tiles of an active segment: each tile's counts
+// become the exclusive prefix within the chunk, and the chunk totals go to
+// ctot.  Four groups of 256 threads (one thread per digit) take a quarter of
+// the chunk's rows each: they sum their rows, add the sums of the groups
+// before them, and write their rows' prefixes (the rows are read twice; the
+// second time from L2).
+constexpr int kScanGroups = 4;
+constexpr int kScanRowsPerGroup = kScanChunk / kScanGroups;
+
+__global__ void __launch_bounds__(k8TPB * kScanGroups) k_tile_scan8(Ctx c, int it) {
     griddep_wait();
+    __shared__ uint32_t part[kScanGroups][k8Bins];
     if (*(volatile int32_t *)c.status)
         return;
     const int cur = it & 1;
     const int A = c.ctr->act_count[cur];
     const int nch = c.ctr->num_chunks[cur];
-    const int d = threadIdx.x;
+    const int d = threadIdx.x & (k8Bins - 1), q = threadIdx.x / k8Bins;
     for (int ch = blockIdx.x; ch < nch; ch += gridDim.x) {
         const int a = upper_index(c.act_chunk_base[cur], A, ch);
         const Seg sg = c.act[cur][a];
         const int lc = ch - c.act_chunk_base[cur][a];
         const int nt = c.act_tile_base[cur][a + 1] - c.act_tile_base[cur][a];
-        const int t0 = lc * kScanChunk, t1 = min(nt, t0 + kScanChunk);
+        const int t0 = lc * kScanChunk + q * kScanRowsPerGroup;
+        const int t1 = min(nt, t0 + kScanRowsPerGroup);  // this group's rows [t0, t1)
         uint32_t *col = c.tcnt[cur] + ((int64_t)sg.row + t0) * k8Bins + d;
-        uint32_t run = 0;
+        const int nr = max(0, t1 - t0);
+        uint32_t sum = 0;
         int t = 0;
-        for (; t + 8 <= t1 - t0; t += 8) {  // eight loads in flight, then the running sum
+        for (; t + 8 <= nr; t += 8) {  // eight loads in flight
+            uint32_t x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                x[u] = col[(int64_t)(t + u) * k8Bins];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                sum += x[u];
+        }
+        for (; t < nr; ++t)
+            sum += col[(int64_t)t * k8Bins];
+        part[q][d] = sum;
+        __syncthreads();
+        uint32_t run = 0, total = 0;
+#pragma unroll
+        for (int g = 0; g < kScanGroups; ++g) {
+            const uint32_t v = part[g][d];
+            run += g < q ? v : 0u;
+            total += v;
+        }
+        t = 0;
+        for (; t + 8 <= nr; t += 8) {
             uint32_t x[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
@@ -211,12 +244,14 @@ __global__ void __launch_bounds__(k8TPB) k_tile_scan8(Ctx c, int it) {
                 run += x[u];
             }
         }
-        for (; t < t1 - t0; ++t) {
+        for (; t < nr; ++t) {
             const uint32_t x = col[(int64_t)t * k8Bins];
             col[(int64_t)t * k8Bins] = run;
             run += x;
         }
-        c.ctot[(int64_t)ch * k8Bins + d] = run;
+        if (q == 0)
+            c.ctot[(int64_t)ch * k8Bins + d] = total;
+        __syncthreads();  // part[] is reused by the next chunk
     }
 }
 
@@ -709,7 +744,7 @@ static void launch_iter8_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     }
     prof_mark("seg_stats", s);
     launch_plan_pending(c, it, s);
-    launch_pdl(k_tile_scan8, dim3(sms * 4), dim3(k8TPB), 0, s, c, it);
+    launch_pdl(k_tile_scan8, dim3(sms * 2), dim3(k8TPB * kScanGroups), 0, s, c, it);
     launch_pdl(k_chunk_scan8, dim3(sblocks), dim3(k8TPB), 0, s, c, it);
     prof_mark("scan", s);
     launch_pdl(k_pass8<KeyT>, dim3(sms * per_sm), dim3(k8TPB), smem, s, c, it);
