@@ -393,6 +393,126 @@ __device__ __forceinline__ int32_t tile_base8(const Ctx &c, int cur, const Tile8
     return gb;
 }
 
+// One tile of the pass: ranking, tile offsets, local scatter and write-out
+// (kWhole: the tile holds k8Tile elements, so no element needs an end check).
+// Returns the output bases of the next tile's digits (loaded meanwhile).
+template <typename KeyT, bool kWhole>
+__device__ __forceinline__ int32_t pass8_tile(const Ctx &c, int cur, Pass8Smem &S, unsigned char *stage, int st,
+                                              bool more, int32_t gb, int tid, int lane, int wid, unsigned lt) {
+    const Tile8 &t = S.tl[st];  // (fields read from shared memory where used)
+    const int lo = t.lo, cnt = kWhole ? k8Tile : t.cnt;
+    const unsigned dmask = (1u << (t.hi - t.lo)) - 1u;
+    const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + t.shk;
+    const int32_t *si = reinterpret_cast<const int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes) + t.shi;
+    bool bad = false;  // an inconsistent count or position (cannot happen): reported, not written
+
+    // ---- ranking within the warp
+    KeyT key[k8Items];
+    int32_t idx[k8Items];
+    uint32_t rnk[k8Items];
+    uint32_t *wc = S.wcnt[wid];
+#pragma unroll
+    for (int i = 0; i < k8Items; ++i) {
+        const int pos = wid * (32 * k8Items) + i * 32 + lane;
+        const bool valid = kWhole || pos < cnt;
+        key[i] = valid ? sk[pos] : (KeyT)0;
+        idx[i] = valid ? si[pos] : 0;
+        const unsigned dig = digit_of<KeyT>(key[i], lo, dmask);
+        // peers: the valid lanes that differ from this one in no digit bit
+        // (bits above a narrower window are 0 everywhere)
+        unsigned diff = 0;
+#pragma unroll
+        for (int b = 0; b < k8Bits; ++b) {
+            const int m = (int)(dig << (31 - b)) >> 31;  // -1 if bit b is set, else 0
+            diff |= __ballot_sync(kFull, m != 0) ^ (unsigned)m;
+        }
+        const unsigned peers = (kWhole ? kFull : __ballot_sync(kFull, valid)) & ~diff;
+        // every lane reads its digit's count; the lowest peer writes it back
+        // advanced (the lowest peers of one group hold distinct digits)
+        const uint32_t before = wc[dig];
+        const unsigned below = peers & lt;
+        if (valid && below == 0)
+            wc[dig] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+        rnk[i] = before + (uint32_t)__popc(below);
+    }
+    __syncthreads();
+    // the next tile's output bases: loads in flight during the rest of this tile
+    const int32_t gb_next = more ? tile_base8(c, cur, S.tl[st ^ 1], tid) : 0;
+    // ---- tile offsets per digit (thread tid = digit), each warp's first slot
+    {
+        uint32_t cw[k8Warps];
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < k8Warps; ++w) {
+            cw[w] = S.wcnt[w][tid];
+            tot += cw[w];
+        }
+        int ttot;
+        uint32_t run = (uint32_t)block_excl_scan((int)tot, &ttot, S.sh);
+        S.gdelta[tid] = gb - (int32_t)run;
+#pragma unroll
+        for (int w = 0; w < k8Warps; ++w) {
+            S.wcnt[w][tid] = run;
+            run += cw[w];
+        }
+    }
+    __syncthreads();
+    // ---- local scatter into the stage buffer (all items are in registers)
+    KeyT *ok = reinterpret_cast<KeyT *>(stage);
+    int32_t *oi = reinterpret_cast<int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes);
+#pragma unroll
+    for (int i = 0; i < k8Items; ++i) {
+        const int pos = wid * (32 * k8Items) + i * 32 + lane;
+        const uint32_t lp = wc[digit_of<KeyT>(key[i], lo, dmask)] + rnk[i];
+        const bool in = lp < (uint32_t)cnt;
+        bad |= (kWhole || pos < cnt) && !in;
+        if ((kWhole || pos < cnt) && in) {
+            ok[lp] = key[i];
+            oi[lp] = idx[i];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int w = 0; w < k8Warps; ++w)  // counters of the next tile
+        S.wcnt[w][tid] = 0;
+    // ---- coalesced write-out: slot j goes to gdelta[its digit] + j
+    const int32_t start = t.start, len = t.len;
+    if (lo == 0 || t.final) {
+#pragma unroll
+        for (int u = 0; u < k8Items; ++u) {
+            const int j = u * k8TPB + tid;
+            if (kWhole || j < cnt) {
+                const int dst = S.gdelta[digit_of<KeyT>(ok[j], lo, dmask)] + j;
+                const bool in = (unsigned)(dst - start) < (unsigned)len;
+                bad |= !in;
+                if (in)
+                    c.F[dst] = oi[j];
+            }
+        }
+    } else {
+        KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(t.buf & 1) ^ 1]);
+        int32_t *oidx = c.idxb[(t.buf & 1) ^ 1];
+#pragma unroll
+        for (int u = 0; u < k8Items; ++u) {
+            const int j = u * k8TPB + tid;
+            if (kWhole || j < cnt) {
+                const KeyT kk = ok[j];
+                const int dst = S.gdelta[digit_of<KeyT>(kk, lo, dmask)] + j;
+                const bool in = (unsigned)(dst - start) < (unsigned)len;
+                bad |= !in;
+                if (in) {
+                    okey[dst] = kk;
+                    oidx[dst] = oi[j];
+                }
+            }
+        }
+    }
+    if (bad)
+        set_status(c.status, kStOverflow);
+    return gb_next;
+}
+
 // Persistent CTAs claim tiles from a counter; the bulk copy of the next tile
 // is in flight, and the output bases of its digits are being loaded, while
 // the current one is ranked and written.  Ranking: for each 32-element group
@@ -476,115 +596,10 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
         phases ^= 1u << st;
         const int gnext = S.nt[st ^ 1];
         const bool more = gnext < T;
-        const Tile8 &t = S.tl[st];  // (fields read from shared memory where used)
-        const int lo = t.lo, cnt = t.cnt;
-        const unsigned dmask = (1u << (t.hi - t.lo)) - 1u;
-        const KeyT *sk = reinterpret_cast<const KeyT *>(stage) + t.shk;
-        const int32_t *si = reinterpret_cast<const int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes) + t.shi;
-
-        // ---- ranking within the warp
-        KeyT key[k8Items];
-        int32_t idx[k8Items];
-        uint32_t rnk[k8Items];
-        uint32_t *wc = S.wcnt[wid];
-#pragma unroll
-        for (int i = 0; i < k8Items; ++i) {
-            const int pos = wid * (32 * k8Items) + i * 32 + lane;
-            const bool valid = pos < cnt;
-            key[i] = valid ? sk[pos] : (KeyT)0;
-            idx[i] = valid ? si[pos] : 0;
-            const unsigned dig = digit_of<KeyT>(key[i], lo, dmask);
-            // peers: the valid lanes that differ from this one in no digit
-            // bit (bits above a narrower window are 0 everywhere)
-            unsigned diff = 0;
-#pragma unroll
-            for (int b = 0; b < k8Bits; ++b) {
-                const int m = (int)(dig << (31 - b)) >> 31;  // -1 if bit b is set, else 0
-                diff |= __ballot_sync(kFull, m != 0) ^ (unsigned)m;
-            }
-            const unsigned peers = __ballot_sync(kFull, valid) & ~diff;
-            // every lane reads its digit's count; the lowest peer writes it
-            // back advanced (the lowest peers of one group hold distinct digits)
-            const uint32_t before = wc[dig];
-            const unsigned below = peers & lt;
-            if (valid && below == 0)
-                wc[dig] = before + (uint32_t)__popc(peers);
-            __syncwarp();
-            rnk[i] = before + (uint32_t)__popc(below);
-        }
-        __syncthreads();
-        // the next tile's output bases: loads in flight during the rest of this tile
-        const int32_t gb_next = more ? tile_base8(c, cur, S.tl[st ^ 1], tid) : 0;
-        // ---- tile offsets per digit (thread tid = digit), each warp's first slot
-        {
-            uint32_t cw[k8Warps];
-            uint32_t tot = 0;
-#pragma unroll
-            for (int w = 0; w < k8Warps; ++w) {
-                cw[w] = S.wcnt[w][tid];
-                tot += cw[w];
-            }
-            int ttot;
-            uint32_t run = (uint32_t)block_excl_scan((int)tot, &ttot, S.sh);
-            S.gdelta[tid] = gb - (int32_t)run;
-#pragma unroll
-            for (int w = 0; w < k8Warps; ++w) {
-                S.wcnt[w][tid] = run;
-                run += cw[w];
-            }
-        }
-        __syncthreads();
-        // ---- local scatter into the stage buffer (all items are in registers)
-        KeyT *ok = reinterpret_cast<KeyT *>(stage);
-        int32_t *oi = reinterpret_cast<int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes);
-#pragma unroll
-        for (int i = 0; i < k8Items; ++i) {
-            const int pos = wid * (32 * k8Items) + i * 32 + lane;
-            if (pos < cnt) {
-                const uint32_t lp = wc[digit_of<KeyT>(key[i], lo, dmask)] + rnk[i];
-                if (lp < (uint32_t)cnt) {
-                    ok[lp] = key[i];
-                    oi[lp] = idx[i];
-                } else {
-                    set_status(c.status, kStOverflow);  // (inconsistent counts: cannot happen)
-                }
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int w = 0; w < k8Warps; ++w)  // counters of the next tile
-            S.wcnt[w][tid] = 0;
-        // ---- coalesced write-out: slot j goes to gdelta[its digit] + j
-        if (lo == 0 || t.final) {
-#pragma unroll
-            for (int u = 0; u < k8Items; ++u) {
-                const int j = u * k8TPB + tid;
-                if (j < cnt) {
-                    const int dst = S.gdelta[digit_of<KeyT>(ok[j], lo, dmask)] + j;
-                    if ((unsigned)(dst - t.start) >= (unsigned)t.len)
-                        set_status(c.status, kStOverflow);
-                    else
-                        c.F[dst] = oi[j];
-                }
-            }
-        } else {
-            KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[(t.buf & 1) ^ 1]);
-            int32_t *oidx = c.idxb[(t.buf & 1) ^ 1];
-#pragma unroll
-            for (int u = 0; u < k8Items; ++u) {
-                const int j = u * k8TPB + tid;
-                if (j < cnt) {
-                    const KeyT kk = ok[j];
-                    const int dst = S.gdelta[digit_of<KeyT>(kk, lo, dmask)] + j;
-                    if ((unsigned)(dst - t.start) >= (unsigned)t.len) {
-                        set_status(c.status, kStOverflow);
-                    } else {
-                        okey[dst] = kk;
-                        oidx[dst] = oi[j];
-                    }
-                }
-            }
-        }
+        // (almost every tile is full: its copy of the code has no end checks)
+        const int32_t gb_next = S.tl[st].cnt == k8Tile
+                                    ? pass8_tile<KeyT, true>(c, cur, S, stage, st, more, gb, tid, lane, wid, lt)
+                                    : pass8_tile<KeyT, false>(c, cur, S, stage, st, more, gb, tid, lane, wid, lt);
         __syncthreads();
         gb = gb_next;
         g = gnext;
