@@ -452,7 +452,9 @@ def run_batched(a, torch, pbit, I, local=0):
                      "steps": a.steps, "graph_nodes": g.node_count(),
                      "timing": "median over the steps; ms_per_step: CUDA events around each graph replay; "
                                "wall_ms_per_step: host clock around launch + status read-back; next[] restored "
-                               "before, outside both"},
+                               "before, outside both",
+                     "structure": "one graph launch per step; its nodes are the memsets and kernels of one "
+                                  "batched sort, each stage a persistent, segmented kernel over all lists"},
            "per_list": {"value": total / (fe / 1e3), "unit": UNIT, "ms": fe, "wall_ms": fw,
                         "timing": "best of 2 loops over all lists; ms: CUDA events before the first and after the "
                                   "last call; wall_ms: host clock over the loop of synchronous calls"},

@@ -613,42 +613,28 @@ struct RelSmem {
     int32_t sv[kRelTile];
     int32_t ss[kRelTile];
     uint16_t sb[kRelTile];
+    int32_t nt[2];                       // the tiles in the two stages (>= tiles: none)
+    alignas(16) int32_t fstage[2][kRelTile + 8];  // F[q0 .. q0 + kRelTile] of each stage (+ the next)
+    alignas(8) uint64_t bar[2];
 };
 
-// Block-wide exclusive scan of one int per thread.
-__device__ int rel_excl_scan(int v, int *total, int *sh /* >= 33 ints */) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o)
-            x += y;
-    }
-    if (lane == 31)
-        sh[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int s = (lane < nw) ? sh[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, s, o);
-            if (lane >= o)
-                s += y;
-        }
-        if (lane < nw)
-            sh[lane] = s;
-        if (lane == 31)
-            sh[32] = s;
-    }
-    __syncthreads();
-    const int base = (wid > 0) ? sh[wid - 1] : 0;
-    *total = sh[32];
-    const int r = base + x - v;
-    __syncthreads();
-    return r;
+// Issue the bulk copy of the order entries F[q0, q0 + kRelTile] that tile g
+// uses (its own and the successor of its last one; fewer at the end of the
+// order) into stage st (one thread).  q0 is a multiple of 4, so the copy
+// starts 16-byte aligned; rounding its length up to 16 bytes stays inside
+// F's 64 bytes of slack.
+__device__ __forceinline__ void relink_issue(const Ctx &c, int g, int st, int32_t nv, RelSmem &S) {
+    const int64_t q0 = (int64_t)g * kRelTile;
+    const int64_t cnt = min((int64_t)kRelTile + 1, (int64_t)nv - q0);
+    const uint32_t bytes = (uint32_t)(((cnt + 3) & ~3ll) * 4);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&S.bar[st], bytes);
+    bulk_g2s(S.fstage[st], c.F + q0, bytes, &S.bar[st]);
 }
 
+// Tiles of kRelTile sorted positions are claimed from a counter one step
+// ahead; the bulk copy engine brings each tile's order entries (and the one
+// after it) into shared memory while the previous tile is bucketed.
 __global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char rel_smem[];
@@ -660,34 +646,62 @@ __global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
     const int L = c.num_lists;
     const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
     const bool doubly = (c.flags & PBIT_DOUBLY) != 0;
+    const int T = (int)((nv + kRelTile - 1) / kRelTile);
     int32_t *tv = c.idxb[0], *ts = c.idxb[1];
-    for (int64_t q0 = (int64_t)blockIdx.x * kRelTile; q0 < nv; q0 += (int64_t)gridDim.x * kRelTile) {
+    int claim = 0;  // thread 0: the tile claimed for the next issue
+    if (threadIdx.x == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        fence_mbar_init();
+        const int g0 = atomicAdd(&c.ctr->rel_ctr.v, 1);
+        S.nt[0] = g0;
+        if (g0 < T) {
+            relink_issue(c, g0, 0, nv, S);
+            claim = atomicAdd(&c.ctr->rel_ctr.v, 1);
+        }
+    }
+    __syncthreads();
+    uint32_t phases = 0;
+    int st = 0;
+    for (int g = S.nt[0]; g < T;) {
+        if (threadIdx.x == 0) {  // the next tile into the other stage, claim the one after
+            S.nt[st ^ 1] = claim;
+            if (claim < T) {
+                relink_issue(c, claim, st ^ 1, nv, S);
+                claim = atomicAdd(&c.ctr->rel_ctr.v, 1);
+            }
+        }
         for (int b = threadIdx.x; b < nb; b += kRelTPB)
             S.cnt[b] = 0;
-        __syncthreads();
-        int32_t vv[kRelItems], ss[kRelItems], rk[kRelItems];
-        // all loads first (independent, in flight together)
-        int32_t f0[kRelItems], f1[kRelItems];
-#pragma unroll
-        for (int i = 0; i < kRelItems; ++i) {
-            const int64_t q = q0 + i * kRelTPB + threadIdx.x;
-            f0[i] = q < nv ? c.F[q] : 0;
-            f1[i] = q + 1 < nv ? c.F[q + 1] : 0;
+        const bool landed = threadIdx.x != 0 || mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
+        if (!__syncthreads_and(landed)) {
+            set_status(c.status, PBIT_ETIMEOUT);
+            if (threadIdx.x == 0) {  // wait (bounded) for the copies still in flight before leaving
+                mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
+                if (S.nt[st ^ 1] < T)
+                    mbar_wait_bounded(&S.bar[st ^ 1], (phases >> (st ^ 1)) & 1u, 1ll << 26);
+            }
+            return;
         }
+        phases ^= 1u << st;
+        const int64_t q0 = (int64_t)g * kRelTile;
+        const int32_t *fs = S.fstage[st];
+        int32_t vv[kRelItems], ss[kRelItems], rk[kRelItems];
 #pragma unroll
         for (int i = 0; i < kRelItems; ++i) {
-            const int64_t q = q0 + i * kRelTPB + threadIdx.x;
+            const int e = i * kRelTPB + threadIdx.x;
+            const int64_t q = q0 + e;
             vv[i] = -1;
             ss[i] = -1;
             if (q < nv) {
                 const int lst = L == 1 ? 0 : upper_index(c.out_base, L, (int32_t)q);
                 const ListDesc &d = c.desc[lst];
-                const int32_t loc = f0[i] - d.out_base;
+                const int32_t loc = fs[e] - d.out_base;
                 const int64_t end = (int64_t)d.out_base + d.n;
                 int32_t succ = -1;
                 bool bad = loc < 0 || loc >= d.n;
                 if (q + 1 < end) {
-                    const int32_t ls = f1[i] - d.out_base;
+                    const int32_t ls = fs[e + 1] - d.out_base;
                     bad |= ls < 0 || ls >= d.n;
                     succ = d.id_base + ls;
                     if (doubly && !bad)
@@ -720,7 +734,7 @@ __global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
                 sum += b < nb ? S.cnt[b] : 0;
             }
             int tot;
-            int ex = rel_excl_scan(sum, &tot, sh);
+            int ex = block_excl_scan(sum, &tot, sh);
             for (int j = 0; j < per; ++j) {
                 const int b = threadIdx.x * per + j;
                 if (b < nb) {
@@ -751,7 +765,9 @@ __global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
             tv[slot] = S.sv[j];
             ts[slot] = S.ss[j];
         }
-        __syncthreads();
+        __syncthreads();  // staging and counts are reused by the next tile
+        g = S.nt[st ^ 1];
+        st ^= 1;
     }
 }
 

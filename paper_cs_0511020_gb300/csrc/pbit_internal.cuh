@@ -79,7 +79,8 @@ struct alignas(128) HotCounter {
 struct Counters {
     HotCounter chunk_next;     // bump allocator of ranking chunks
     HotCounter task_next;      // work counter of the ranking walk
-    HotCounter fin_ctr;        // work counter of the finish kernel
+    HotCounter fin_ctr;        // work counter of the CTA finish
+    HotCounter rel_ctr;        // work counter of the relink partition
     int32_t n_virt;            // total nodes over all lists
     int32_t fin_count;
     int32_t mid_count;         // buckets finished by one CTA each
