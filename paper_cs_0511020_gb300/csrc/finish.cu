@@ -335,12 +335,11 @@ __global__ void __launch_bounds__(32 * kFWarps) k_finish(Ctx c) {
 // bits that vary in it (one window for spans up to 8 bits, two up to 16),
 // and writes the node ids to F.  A window is a stable counting split: each
 // warp ranks its contiguous slice of the bucket group by group (32 elements:
-// the lanes holding the same digit are found with one ballot per digit bit,
-// each reads the warp's shared counter of that digit and the lowest of them
-// writes it back advanced by the group's count), one thread per digit then turns
-// the (warp, digit) counts into each warp's first slot (digit-major, warps in
-// slice order: stable), and every element moves to its slot in the other
-// buffer.  This replaces the further global passes, their planning and the
+// the lanes holding the same digit find each other through a per-warp table
+// of peer masks and counts in shared memory, warp_rank_by_or), one thread per
+// digit then turns the (warp, digit) counts into each warp's first slot
+// (digit-major, warps in slice order: stable), and every element moves to its
+// slot in the other buffer.  This replaces the further global passes, their planning and the
 // small-bucket finish that such a bucket would otherwise go through.
 constexpr int kMidTPB = 256;
 constexpr int kMidWarps = kMidTPB / 32;
@@ -358,8 +357,11 @@ struct MidLayout {
     static constexpr int kMinBlocks = sizeof(KeyT) == 8 ? 2 : 3;
 };
 
+static_assert(kMidWarps * kMidBins * (int)sizeof(uint2) <= MidLayout<uint8_t>::kBuf,
+              "the ranking table fits in a bucket buffer");
+
 struct MidSmem {
-    uint32_t wcnt[kMidWarps][kMidBins];
+    uint32_t wcnt[kMidWarps][kMidBins];  // per warp and digit: the warp's first slot
     int sh[40];
     unsigned long long s_and, s_or;
     int32_t next;  // bucket claimed next
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
     if (*(volatile int32_t *)c.status)
         return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned lt = lanemask_lt();
+    const unsigned lt = lanemask_lt(), lane_bit = 1u << lane;
     const int nmid = c.ctr->mid_count;
     unsigned char *bufA = msm, *bufB = msm + L::kBuf;
     if (tid == 0) {
@@ -384,9 +386,6 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
         fence_mbar_init();
         S.next = atomicAdd(&c.ctr->fin_ctr.v, 1);
     }
-#pragma unroll
-    for (int w = 0; w < kMidWarps; ++w)
-        S.wcnt[w][tid] = 0;
     __syncthreads();
     uint32_t phase = 0;
     long long my_elems = 0;
@@ -463,10 +462,18 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
             const int width = (span + nwin - 1) / nwin;
             const int nitems = (len + kMidTPB - 1) / kMidTPB;  // groups per warp slice
             const int s0 = wid * 32 * nitems;
+            unsigned char *dst_buf = bufB, *src_buf = bufA;
             for (int w = 0; w < nwin; ++w) {
                 const int wl = lv + w * width;
                 const unsigned dmask = (1u << min(width, hv + 1 - wl)) - 1u;
                 const bool last = w == nwin - 1;
+                // the ranking's {peer mask, count} table lives in the window's
+                // destination buffer, which is written only after the ranking
+                uint2 *tab = reinterpret_cast<uint2 *>(dst_buf);
+#pragma unroll
+                for (int e = tid; e < kMidWarps * kMidBins / 2; e += kMidTPB)
+                    reinterpret_cast<uint4 *>(tab)[e] = make_uint4(0u, 0u, 0u, 0u);
+                __syncthreads();
                 uint32_t rnk[kMidItems];
 #pragma unroll
                 for (int i = 0; i < kMidItems; ++i) {
@@ -475,22 +482,7 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
                         const int pos = s0 + i * 32 + lane;
                         const bool valid = pos < len;
                         const unsigned dig = valid ? digit_of<KeyT>(ka[pos], wl, dmask) : 0u;
-                        unsigned diff = 0;
-#pragma unroll
-                        for (int b = 0; b < kMidBits; ++b) {
-                            const int mb = (int)(dig << (31 - b)) >> 31;  // -1 if bit b is set, else 0
-                            diff |= __ballot_sync(kFull, mb != 0) ^ (unsigned)mb;
-                        }
-                        const unsigned peers = __ballot_sync(kFull, valid) & ~diff;
-                        // every lane reads its digit's count; the lowest peer
-                        // writes it back advanced (peers share one digit, other
-                        // lowest peers write other counters)
-                        const uint32_t before = S.wcnt[wid][dig];
-                        const unsigned below = peers & lt;
-                        if (valid && below == 0)
-                            S.wcnt[wid][dig] = before + (uint32_t)__popc(peers);
-                        __syncwarp();
-                        rnk[i] = before + (uint32_t)__popc(below);
+                        rnk[i] = warp_rank_by_or(tab + wid * kMidBins, dig, valid, lane_bit, lt);
                     }
                 }
                 __syncthreads();
@@ -499,7 +491,7 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
                     uint32_t tot = 0;
 #pragma unroll
                     for (int x = 0; x < kMidWarps; ++x) {
-                        cw[x] = S.wcnt[x][tid];
+                        cw[x] = tab[x * kMidBins + tid].y;
                         tot += cw[x];
                     }
                     int ttot;
@@ -510,7 +502,7 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
                         run += cw[x];
                     }
                 }
-                __syncthreads();
+                __syncthreads();  // (the table is read: the scatter may overwrite it)
 #pragma unroll
                 for (int i = 0; i < kMidItems; ++i) {
                     if (i < nitems) {
@@ -528,11 +520,7 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
                         }
                     }
                 }
-                __syncthreads();
-#pragma unroll
-                for (int x = 0; x < kMidWarps; ++x)  // counters of the next window
-                    S.wcnt[x][tid] = 0;
-                __syncthreads();  // zeroed before any warp ranks the next window
+                __syncthreads();  // the scatter is complete before the next window ranks
                 res = ib;
                 KeyT *tk = ka;  // the other buffer is the next window's source
                 ka = kb;
@@ -540,6 +528,9 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
                 int32_t *ti = ia;
                 ia = ib;
                 ib = ti;
+                unsigned char *tb = src_buf;
+                src_buf = dst_buf;
+                dst_buf = tb;
             }
         }
         int32_t *dst = c.F + f.start;

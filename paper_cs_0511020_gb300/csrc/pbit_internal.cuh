@@ -255,6 +255,30 @@ __device__ __forceinline__ int block_excl_scan(int v, int *total, int *sh /* >= 
     return r;
 }
 
+// Stable rank of one lane's element among the elements of its 32-element
+// group and of the warp's earlier groups that carry the same digit.  tab is
+// the warp's table in shared memory, one {peer mask, running count} pair per
+// digit, all masks zero on entry.  Each valid lane ORs its bit into its
+// digit's mask; after the warp has synchronised the mask holds exactly the
+// lanes with that digit (its peers).  Every peer reads the pair, and the
+// lowest peer writes it back with the mask cleared and the count advanced by
+// the number of peers; the lowest peers of one group hold distinct digits.
+// Memory order = group, lane, so the rank is stable.  All lanes of the warp
+// call it together; invalid lanes take part without an element.
+__device__ __forceinline__ uint32_t warp_rank_by_or(uint2 *tab, unsigned dig, bool valid, unsigned lane_bit,
+                                                    unsigned lt) {
+    if (valid)
+        atomicOr(&tab[dig].x, lane_bit);
+    __syncwarp();
+    const uint2 e = tab[dig];
+    const unsigned below = e.x & lt;
+    __syncwarp();  // every peer has read the pair before it is rewritten
+    if (valid && below == 0)
+        tab[dig] = make_uint2(0u, e.y + (uint32_t)__popc(e.x));
+    __syncwarp();
+    return e.y + (uint32_t)__popc(below);
+}
+
 
 // Keys up to 32 bits are handled in 32-bit words (digit shifts, AND/OR).
 template <typename KeyT>
