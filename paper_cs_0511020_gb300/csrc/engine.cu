@@ -43,6 +43,7 @@ struct ProfState {
     int64_t n = 0, rcap = 0, scap = 0, rounds = 0;
     int kb = 4;
     bool blocked_relink = false;
+    bool emit_hist = false;  // the emit counted the first pass's digits (its time is the emit's)
     bool pack = false;
     bool small = false;
 };
@@ -246,6 +247,12 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     x.chunk_j0 = (int32_t *)take(4 * (size_t)z.chunk_cap);
     x.chunk_data = (int32_t *)take(4 * (size_t)z.chunk_cap * z.CH);
     x.chunk_key = take((size_t)z.kb * z.chunk_cap * z.CH);
+    x.blk_cap = (z.ncap + kEmitBlock - 1) / kEmitBlock + 1;
+    x.chunk_pc = (int2 *)take(8 * (size_t)z.chunk_cap);
+    x.blk_cnt = (int32_t *)take(4 * (size_t)x.blk_cap);
+    zero(x.blk_cnt, 0, 4 * (size_t)x.blk_cap);
+    x.blk_start = (int32_t *)take(4 * (size_t)(x.blk_cap + 1));
+    x.blk_list = (int2 *)take(16 * (size_t)z.chunk_cap);
     // keyb[1], idxb[1] and F are adjacent: the ranking's pack array spans
     // them (n * (kb + 8) bytes >= n * 8, and >= n * 16 when kb == 8)
     for (int b = 0; b < 2; ++b) {
@@ -327,6 +334,15 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     prof_mark("memset", s);
     Ctx cc = c;
     cc.M = M;
+    // One list that starts the 256-bucket passes: the emit counts the first
+    // pass's digits per tile (the list's tiles are the emit's blocks), so the
+    // first histogram kernel is left out.  The test mirrors plan_init's.
+    cc.emit_hist = 0;
+    if (mode == 2 && tmpl && cc.num_lists == 1 && cc.D > digit_bits() && !cc.force_pass) {
+        const int64_t nl = tmpl->n;
+        const bool mid = nl <= kMidCap && M <= kMidSpan;
+        cc.emit_hist = (nl > cc.cutoff && !mid) ? 1 : 0;
+    }
     launch_setup(cc, d_offsets, d_roots, mode, tmpl, s, sms);
     if (small_lists && mode != 0) {
         NvtxRange r("pbit_short_lists");
@@ -353,7 +369,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     }
     if (stop_after == 1)
         return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
-    n += 8 + rounds;
+    n += 11 + rounds - cc.emit_hist;  // (the emit is four kernels)
     const int iters = (M + cc.D - 1) / cc.D;
     {
         NvtxRange r("pbit_msd_passes");
@@ -377,6 +393,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
         g_prof.rounds = rounds;
         g_prof.kb = cc.key_bytes;
         g_prof.blocked_relink = relink_blocked(cc);
+        g_prof.emit_hist = cc.emit_hist != 0;
         g_prof.pack = cc.pack != nullptr;
     }
     if (launches)
@@ -676,7 +693,7 @@ int32_t pbit_profile_read(pbit_kernel_stat *out, int32_t max) {
                 // pointer jumping over the walks; expand: read both, write one
                 b = (double)g_prof.rcap * (16.0 + 24.0) + (double)g_prof.scap * 24.0 * (double)g_prof.rounds;
             } else if (!std::strcmp(nm, "seg_stats")) {
-                for (int it = 0; it < kMaxIters; ++it)
+                for (int it = g_prof.emit_hist ? 1 : 0; it < kMaxIters; ++it)
                     b += (double)k.stat_elems[it] * kb;
             } else if (!std::strcmp(nm, "pass")) {
                 for (int it = 0; it < kMaxIters; ++it)

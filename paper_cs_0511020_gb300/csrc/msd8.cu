@@ -751,7 +751,7 @@ static void launch_iter8_t(const Ctx &c, int it, cudaStream_t s, int sms) {
     const int per_sm = Pass8Layout<KeyT>::kMinBlocks;
     const unsigned wblocks = (unsigned)max(1, min(sms * 8, (int)((c.seg_cap + 7) / 8)));  // 8 warps per CTA
     const unsigned sblocks = (unsigned)max(1, min(sms * 8, (int)c.seg_cap));
-    {
+    if (it > 0 || !c.emit_hist) {  // (emit_hist: the emit counted the first pass's tiles)
         const int hsmem = Hist8Layout<KeyT>::kTotal;
         cudaFuncSetAttribute(k_hist8<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, hsmem);
         const int per_sm = max(1, min(8, (200 * 1024) / (hsmem + 1024)));

@@ -67,6 +67,11 @@ constexpr int kSmallList = 4096;  // ... when at most this many of their key bit
 // Elements per MSD pass tile (4- and 8-bit passes alike) and tiles per scan
 // chunk: the plan kernels count tiles and chunks in these units.
 constexpr int kPassTile = 2048;
+// List positions per emit block (one block = one statistics tile of a list
+// that starts at position 0).
+constexpr int kEmitLog2 = 11;
+constexpr int kEmitBlock = 1 << kEmitLog2;
+static_assert(kEmitBlock == kPassTile, "an emit block is one pass tile");
 constexpr int kScanChunk = 256;
 
 // Work counters that many CTAs hit at once sit on their own 128-byte lines
@@ -139,6 +144,14 @@ struct Ctx {
     int32_t *chunk_j0;
     int32_t *chunk_data;        // chunk_cap x CH node ids (virtual positions)
     unsigned char *chunk_key;   // chunk_cap x CH sort keys
+    // emit: the chunks grouped by the block of kEmitBlock list positions
+    // they fill (a chunk that runs into the next block is listed in both)
+    int2 *chunk_pc;             // chunk_cap: {first list position, entries} (-1, 0: unused)
+    int32_t *blk_cnt;           // blk_cap: chunks per block, then the fill cursors
+    int32_t *blk_start;         // blk_cap + 1: first list entry of each block
+    int2 *blk_list;             // 2 x chunk_cap: {chunk, (first position - block start + 32) | entries << 12}
+    int64_t blk_cap;
+    int32_t emit_hist;          // 1: the emit also counts the first 256-bucket pass's digits per tile
     unsigned char *keyb[2];
     int32_t *idxb[2];
     int32_t *F;

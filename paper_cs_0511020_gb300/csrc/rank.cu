@@ -477,73 +477,263 @@ __global__ void k_validate(Ctx c) {
     }
 }
 
-// Each warp moves 32 chunks: lane l first fetches the metadata of chunk l
-// (task, offset in the task, the task's list and rank) so the dependent
-// metadata loads of 32 chunks overlap; then the chunks are copied kEmitBatch
-// at a time with all loads issued before the stores (the kernel is bound by
-// load latency: more loads in flight per warp).
-constexpr int kEmitBatch = 8;
-template <typename KeyT>
-__global__ void __launch_bounds__(256) k_emit(Ctx c) {
+// The emit writes the list-order arrays block by block: each block of
+// kEmitBlock list positions is gathered from the chunks that fill it into
+// shared memory and written out as whole lines (chunks land at random
+// places, so writing each chunk where it belongs would leave partly written
+// sectors that L2 must fill from DRAM).  First every chunk gets its place
+// and the chunks are grouped by block (count, scan, fill).
+
+// Step 1: each used chunk's first list position and entry count (its task's
+// rank + its offset in the task), and the chunks per block; a chunk that
+// runs past the end of its block is counted for the next block too.
+__global__ void __launch_bounds__(256) k_chunk_place(Ctx c) {
     griddep_wait();
     if (*(volatile int32_t *)c.status)
         return;
-    const int lane = threadIdx.x & 31;
-    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t nchunks = min((int64_t)c.ctr->chunk_next.v, c.chunk_cap);
     const int64_t *w = c.wy[0];
+    const int32_t CH = c.CH;
+    for (int64_t mc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; mc < nchunks;
+         mc += (int64_t)gridDim.x * blockDim.x) {
+        int2 pc = make_int2(-1, 0);
+        const int32_t t = c.chunk_task[mc];
+        if (t >= 0) {
+            const int32_t j0 = c.chunk_j0[mc];
+            const int32_t len = c.task_len[t];
+            const int32_t lst = c.task_list[t];
+            const uint32_t suffix = (uint32_t)((uint64_t)w[t]);
+            const int32_t n = c.desc[lst].n, ob = c.desc[lst].out_base;
+            const int32_t cnt = min(CH, len - j0);
+            const int64_t pos0 = (int64_t)ob + ((int64_t)n - (int64_t)suffix) + j0;
+            if (cnt > 0) {
+                if (pos0 < ob || pos0 + cnt > (int64_t)ob + n) {
+                    set_status(c.status, PBIT_EBADLIST);
+                } else {
+                    pc = make_int2((int32_t)pos0, cnt);
+                    const int64_t bk = pos0 >> kEmitLog2;
+                    atomicAdd(&c.blk_cnt[bk], 1);
+                    if (((pos0 + cnt - 1) >> kEmitLog2) != bk)
+                        atomicAdd(&c.blk_cnt[bk + 1], 1);
+                }
+            }
+        }
+        c.chunk_pc[mc] = pc;
+    }
+}
+
+// Step 2 (one CTA): blk_start = exclusive prefix of the counts; the counts
+// are reset to serve as the fill cursors.
+__global__ void __launch_bounds__(1024) k_blk_scan(Ctx c) {
+    griddep_wait();
+    __shared__ int sh[40];
+    __shared__ int s_base;
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int64_t nblk = ((int64_t)c.ctr->n_virt + kEmitBlock - 1) >> kEmitLog2;
+    if (threadIdx.x == 0)
+        s_base = 0;
+    __syncthreads();
+    constexpr int kPer = 8;  // consecutive blocks per thread and round
+    for (int64_t r0 = 0; r0 < nblk; r0 += (int64_t)blockDim.x * kPer) {
+        const int64_t b0 = r0 + (int64_t)threadIdx.x * kPer;
+        int v[kPer];
+        int sum = 0;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            v[u] = b0 + u < nblk ? c.blk_cnt[b0 + u] : 0;
+            sum += v[u];
+        }
+        int tot;
+        int run = s_base + block_excl_scan(sum, &tot, sh);
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            if (b0 + u < nblk) {
+                c.blk_start[b0 + u] = run;
+                c.blk_cnt[b0 + u] = 0;
+            }
+            run += v[u];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            s_base += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        c.blk_start[nblk] = s_base;
+}
+
+// Step 3: every chunk is entered in the list of each block it fills, with
+// its first position relative to the block (+ 32, so a chunk that began in
+// the block before stays positive) and its entry count.
+__device__ __forceinline__ void blk_enter(const Ctx &c, int64_t bk, int64_t mc, int64_t pos0, int cnt) {
+    const int64_t slot = (int64_t)c.blk_start[bk] + atomicAdd(&c.blk_cnt[bk], 1);
+    const int rel = (int)(pos0 - (bk << kEmitLog2)) + 32;
+    if (slot < (int64_t)c.blk_start[bk + 1] && slot < 2 * c.chunk_cap)
+        c.blk_list[slot] = make_int2((int32_t)mc, rel | (cnt << 12));
+    else
+        set_status(c.status, kStOverflow);  // (inconsistent counts: cannot happen)
+}
+
+__global__ void __launch_bounds__(256) k_chunk_fill(Ctx c) {
+    griddep_wait();
+    if (*(volatile int32_t *)c.status)
+        return;
+    const int64_t nchunks = min((int64_t)c.ctr->chunk_next.v, c.chunk_cap);
+    for (int64_t mc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; mc < nchunks;
+         mc += (int64_t)gridDim.x * blockDim.x) {
+        const int2 pc = c.chunk_pc[mc];
+        if (pc.x < 0)
+            continue;
+        const int64_t bk = (int64_t)pc.x >> kEmitLog2;
+        blk_enter(c, bk, mc, pc.x, pc.y);
+        if ((((int64_t)pc.x + pc.y - 1) >> kEmitLog2) != bk)
+            blk_enter(c, bk + 1, mc, pc.x, pc.y);
+    }
+}
+
+// Step 4: one CTA per block of kEmitBlock positions.  Each warp takes its
+// share of the block's chunk list kEmitBatch chunks at a time (lane u holds
+// the u-th entry; every chunk's 32 entries are read by the whole warp, all
+// loads in flight before the shared-memory stores), then the block is
+// written to (ord_key, ord_idx) with 16-byte stores.  kHist (one list at
+// position 0 on the 256-bucket passes): the CTA also counts the digits of the
+// first pass's window [max(M - D, 0), M) and the AND/OR of the keys, as the
+// first histogram kernel would (row b of the counts = tile b of the list).
+constexpr int kEmitWarps = 8;
+constexpr int kEmitBatch = 8;
+
+template <typename KeyT, bool kHist>
+__global__ void __launch_bounds__(32 * kEmitWarps) k_emit_blk(Ctx c) {
+    griddep_wait();
+    __shared__ __align__(16) KeyT sk[kEmitBlock];
+    __shared__ __align__(16) int32_t si[kEmitBlock];
+    __shared__ uint32_t sh_h[kHist ? kEmitWarps : 1][256];
+    __shared__ unsigned long long s_and, s_or;
+    if (*(volatile int32_t *)c.status)
+        return;
+    using U = typename KeyWord<KeyT>::U;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t nv = c.ctr->n_virt;
+    const int64_t nblk = (nv + kEmitBlock - 1) >> kEmitLog2;
     const KeyT *ckey = reinterpret_cast<const KeyT *>(c.chunk_key);
     KeyT *okey = reinterpret_cast<KeyT *>(c.keyb[0]);
     int32_t *oidx = c.idxb[0];
-    const int CH = c.CH;  // == 32
-    for (int64_t ch0 = gwarp * 32; ch0 < nchunks; ch0 += nwarps * 32) {
-        // per-lane metadata of chunk ch0 + lane
-        int32_t m_pos = 0, m_cnt = 0;
-        const int64_t mc = ch0 + lane;
-        if (mc < nchunks) {
-            const int32_t t = c.chunk_task[mc];
-            if (t >= 0) {
-                const int32_t j0 = c.chunk_j0[mc];
-                const int32_t len = c.task_len[t];
-                const int32_t lst = c.task_list[t];
-                const uint32_t suffix = (uint32_t)((uint64_t)w[t]);
-                const int32_t n = c.desc[lst].n, ob = c.desc[lst].out_base;
-                m_cnt = min(CH, len - j0);
-                const int64_t pos0 = (int64_t)ob + ((int64_t)n - (int64_t)suffix) + j0;
-                if (pos0 < ob || pos0 + m_cnt > (int64_t)ob + n) {
-                    set_status(c.status, PBIT_EBADLIST);
-                    m_cnt = 0;
-                }
-                m_pos = (int32_t)pos0;
-            }
+    const int32_t CH = c.CH;
+    int lo = 0;
+    unsigned dmask = 0;
+    if constexpr (kHist) {
+        lo = max(c.M - c.D, 0);
+        dmask = (1u << (c.M - lo)) - 1u;
+#pragma unroll
+        for (int x = 0; x < kEmitWarps; ++x)
+            sh_h[x][tid] = 0;
+        if (tid == 0) {
+            s_and = ~0ull;
+            s_or = 0ull;
         }
-        const int nc = (int)min((int64_t)32, nchunks - ch0);
-        for (int b = 0; b < nc; b += kEmitBatch) {
-            int32_t vi[kEmitBatch];
-            KeyT vk[kEmitBatch];
-            int32_t pos[kEmitBatch];
-            bool ok[kEmitBatch];
+        __syncthreads();
+    }
+    long long my_elems = 0;
+    for (int64_t bk = blockIdx.x; bk < nblk; bk += gridDim.x) {
+        const int64_t p0 = bk << kEmitLog2;
+        const int cnt_b = (int)min((int64_t)kEmitBlock, nv - p0);
+        const int l0 = c.blk_start[bk], nl = c.blk_start[bk + 1] - l0;
+        for (int k0 = wid; k0 < nl; k0 += kEmitWarps * kEmitBatch) {
+            int2 e = make_int2(-1, 0);
+            if (lane < kEmitBatch) {
+                const int k = k0 + lane * kEmitWarps;
+                if (k < nl)
+                    e = c.blk_list[l0 + k];
+            }
+            KeyT kv[kEmitBatch];
+            int32_t iv[kEmitBatch];
+            int sp[kEmitBatch];
 #pragma unroll
             for (int u = 0; u < kEmitBatch; ++u) {
-                const int src = min(b + u, 31);
-                const int32_t cnt = __shfl_sync(kFull, m_cnt, src);
-                pos[u] = __shfl_sync(kFull, m_pos, src) + lane;
-                ok[u] = (b + u < nc) && lane < cnt;
-                if (ok[u]) {
-                    const int64_t e = (ch0 + b + u) * CH + lane;
-                    vi[u] = c.chunk_data[e];
-                    vk[u] = ckey[e];
+                const int m = __shfl_sync(kFull, e.x, u);
+                const int pk = __shfl_sync(kFull, e.y, u);
+                const int rel = (pk & 0xfff) - 32 + lane;  // this lane's position in the block
+                const bool ok = m >= 0 && lane < (pk >> 12) && rel >= 0 && rel < cnt_b;
+                sp[u] = ok ? rel : -1;
+                if (ok) {
+                    kv[u] = ckey[(int64_t)m * CH + lane];
+                    iv[u] = c.chunk_data[(int64_t)m * CH + lane];
                 }
             }
 #pragma unroll
             for (int u = 0; u < kEmitBatch; ++u) {
-                if (ok[u]) {
-                    okey[pos[u]] = vk[u];
-                    oidx[pos[u]] = vi[u];
+                if (sp[u] >= 0) {
+                    sk[sp[u]] = kv[u];
+                    si[sp[u]] = iv[u];
                 }
             }
         }
+        __syncthreads();
+        my_elems += cnt_b;
+        if constexpr (kHist) {
+            U a_and = ~(U)0, a_or = 0;
+#pragma unroll
+            for (int u = 0; u < kEmitBlock / (32 * kEmitWarps); ++u) {
+                const int j = u * 32 * kEmitWarps + tid;
+                if (j < cnt_b) {
+                    const U kk = (U)sk[j];
+                    a_and &= kk;
+                    a_or |= kk;
+                    atomicAdd(&sh_h[wid][(unsigned)(kk >> lo) & dmask], 1u);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a_and &= __shfl_xor_sync(kFull, a_and, o);
+                a_or |= __shfl_xor_sync(kFull, a_or, o);
+            }
+            if (lane == 0) {  // keys are zero-extended to 64 bits
+                atomicAnd(&s_and, (unsigned long long)a_and);
+                atomicOr(&s_or, (unsigned long long)a_or);
+            }
+        }
+        // write-out: whole blocks with 16-byte stores, the last one element-wise
+        if (cnt_b == kEmitBlock) {
+            constexpr int kKeyVec = kEmitBlock * (int)sizeof(KeyT) / 16;
+            const uint4 *vk = reinterpret_cast<const uint4 *>(sk);
+            uint4 *dk = reinterpret_cast<uint4 *>(okey + p0);
+            for (int v = tid; v < kKeyVec; v += 32 * kEmitWarps)
+                dk[v] = vk[v];
+            const uint4 *vi = reinterpret_cast<const uint4 *>(si);
+            uint4 *di = reinterpret_cast<uint4 *>(oidx + p0);
+            for (int v = tid; v < kEmitBlock / 4; v += 32 * kEmitWarps)
+                di[v] = vi[v];
+        } else {
+            for (int j = tid; j < cnt_b; j += 32 * kEmitWarps) {
+                okey[p0 + j] = sk[j];
+                oidx[p0 + j] = si[j];
+            }
+        }
+        __syncthreads();
+        if constexpr (kHist) {
+            uint32_t sum = 0;
+#pragma unroll
+            for (int x = 0; x < kEmitWarps; ++x) {
+                sum += sh_h[x][tid];
+                sh_h[x][tid] = 0;
+            }
+            if (bk < c.row_cap)
+                c.tcnt[0][bk * 256 + tid] = sum;
+            else
+                set_status(c.status, kStOverflow);
+            if (tid == 0) {
+                atomicAnd(&c.pand[0][0], s_and);
+                atomicOr(&c.por[0][0], s_or);
+                s_and = ~0ull;
+                s_or = 0ull;
+            }
+            __syncthreads();  // counters and AND/OR reset before the next block counts
+        }
+    }
+    if constexpr (kHist) {
+        if (tid == 0 && my_elems)
+            atomicAdd((unsigned long long *)&c.ctr->stat_elems[0], (unsigned long long)my_elems);
     }
 }
 
@@ -606,12 +796,26 @@ void launch_wyllie(const Ctx &c, cudaStream_t s, int sms, int rounds) {
 void launch_validate_emit(const Ctx &c, cudaStream_t s, int sms) {
     launch_pdl(k_validate, dim3(max(1, min(sms, (c.num_lists + 255) / 256))), dim3(256), 0, s, c);
     prof_mark("validate", s);
-    unsigned blocks = (unsigned)(sms * 8);
-    switch (c.key_bytes) {
-    case 1: launch_pdl(k_emit<uint8_t>, dim3(blocks), dim3(256), 0, s, c); break;
-    case 2: launch_pdl(k_emit<uint16_t>, dim3(blocks), dim3(256), 0, s, c); break;
-    case 4: launch_pdl(k_emit<uint32_t>, dim3(blocks), dim3(256), 0, s, c); break;
-    default: launch_pdl(k_emit<unsigned long long>, dim3(blocks), dim3(256), 0, s, c); break;
+    const unsigned cb = (unsigned)max((int64_t)1, min((int64_t)sms * 8, (c.chunk_cap + 255) / 256));
+    launch_pdl(k_chunk_place, dim3(cb), dim3(256), 0, s, c);
+    launch_pdl(k_blk_scan, dim3(1), dim3(1024), 0, s, c);
+    launch_pdl(k_chunk_fill, dim3(cb), dim3(256), 0, s, c);
+    const unsigned eb = (unsigned)max((int64_t)1, min((int64_t)sms * 8, c.blk_cap));
+    const dim3 et(32 * kEmitWarps);
+    if (c.emit_hist) {
+        switch (c.key_bytes) {
+        case 1: launch_pdl(k_emit_blk<uint8_t, true>, dim3(eb), et, 0, s, c); break;
+        case 2: launch_pdl(k_emit_blk<uint16_t, true>, dim3(eb), et, 0, s, c); break;
+        case 4: launch_pdl(k_emit_blk<uint32_t, true>, dim3(eb), et, 0, s, c); break;
+        default: launch_pdl(k_emit_blk<unsigned long long, true>, dim3(eb), et, 0, s, c); break;
+        }
+    } else {
+        switch (c.key_bytes) {
+        case 1: launch_pdl(k_emit_blk<uint8_t, false>, dim3(eb), et, 0, s, c); break;
+        case 2: launch_pdl(k_emit_blk<uint16_t, false>, dim3(eb), et, 0, s, c); break;
+        case 4: launch_pdl(k_emit_blk<uint32_t, false>, dim3(eb), et, 0, s, c); break;
+        default: launch_pdl(k_emit_blk<unsigned long long, false>, dim3(eb), et, 0, s, c); break;
+        }
     }
     prof_mark("emit", s);
 }
