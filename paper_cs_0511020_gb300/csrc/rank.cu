@@ -523,7 +523,8 @@ __global__ void __launch_bounds__(256) k_chunk_place(Ctx c) {
 }
 
 // Step 2 (one CTA): blk_start = exclusive prefix of the counts; the counts
-// are reset to serve as the fill cursors.
+// are reset to serve as the fill cursors.  Each thread takes 32 consecutive
+// counts per round (eight 16-byte loads, all in flight).
 __global__ void __launch_bounds__(1024) k_blk_scan(Ctx c) {
     griddep_wait();
     __shared__ int sh[40];
@@ -534,25 +535,53 @@ __global__ void __launch_bounds__(1024) k_blk_scan(Ctx c) {
     if (threadIdx.x == 0)
         s_base = 0;
     __syncthreads();
-    constexpr int kPer = 8;  // consecutive blocks per thread and round
+    constexpr int kPer = 32;
     for (int64_t r0 = 0; r0 < nblk; r0 += (int64_t)blockDim.x * kPer) {
         const int64_t b0 = r0 + (int64_t)threadIdx.x * kPer;
         int v[kPer];
         int sum = 0;
+        if (b0 + kPer <= nblk) {  // (blk_cnt is 256-byte aligned: b0 is a multiple of 32)
+            const int4 *q = reinterpret_cast<const int4 *>(c.blk_cnt + b0);
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            v[u] = b0 + u < nblk ? c.blk_cnt[b0 + u] : 0;
-            sum += v[u];
+            for (int u = 0; u < kPer / 4; ++u) {
+                const int4 x = q[u];
+                v[4 * u] = x.x;
+                v[4 * u + 1] = x.y;
+                v[4 * u + 2] = x.z;
+                v[4 * u + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < kPer; ++u)
+                v[u] = b0 + u < nblk ? c.blk_cnt[b0 + u] : 0;
         }
+#pragma unroll
+        for (int u = 0; u < kPer; ++u)
+            sum += v[u];
         int tot;
         int run = s_base + block_excl_scan(sum, &tot, sh);
 #pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            if (b0 + u < nblk) {
-                c.blk_start[b0 + u] = run;
-                c.blk_cnt[b0 + u] = 0;
+        for (int u = 0; u < kPer; ++u) {  // counts -> starts
+            const int x = v[u];
+            v[u] = run;
+            run += x;
+        }
+        if (b0 + kPer <= nblk) {
+            int4 *qs = reinterpret_cast<int4 *>(c.blk_start + b0);
+            int4 *qc = reinterpret_cast<int4 *>(c.blk_cnt + b0);
+#pragma unroll
+            for (int u = 0; u < kPer / 4; ++u) {
+                qs[u] = make_int4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+                qc[u] = make_int4(0, 0, 0, 0);
             }
-            run += v[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < kPer; ++u) {
+                if (b0 + u < nblk) {
+                    c.blk_start[b0 + u] = v[u];
+                    c.blk_cnt[b0 + u] = 0;
+                }
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0)
@@ -593,9 +622,11 @@ __global__ void __launch_bounds__(256) k_chunk_fill(Ctx c) {
 }
 
 // Step 4: one CTA per block of kEmitBlock positions.  Each warp takes its
-// share of the block's chunk list kEmitBatch chunks at a time (lane u holds
-// the u-th entry; every chunk's 32 entries are read by the whole warp, all
-// loads in flight before the shared-memory stores), then the block is
+// share of the block's chunk list (lane u holds the u-th entry; every
+// chunk's 32 entries are read by the whole warp): with keys of 4 or 8 bytes
+// by asynchronous copies into shared memory, all in flight at once, else
+// kEmitBatch chunks at a time with the loads issued before the shared-memory
+// stores.  Then the block is
 // written to (ord_key, ord_idx) with 16-byte stores.  kHist (one list at
 // position 0 on the 256-bucket passes): the CTA also counts the digits of the
 // first pass's window [max(M - D, 0), M) and the AND/OR of the keys, as the
@@ -639,7 +670,27 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit_blk(Ctx c) {
         const int64_t p0 = bk << kEmitLog2;
         const int cnt_b = (int)min((int64_t)kEmitBlock, nv - p0);
         const int l0 = c.blk_start[bk], nl = c.blk_start[bk + 1] - l0;
-        for (int k0 = wid; k0 < nl; k0 += kEmitWarps * kEmitBatch) {
+        if constexpr (sizeof(KeyT) >= 4) {
+            // keys of 4 or 8 bytes: asynchronous copies straight into shared
+            // memory, so every chunk of the warp's share is in flight at once
+            for (int k0 = wid; k0 < nl; k0 += kEmitWarps * 32) {
+                const int k = k0 + lane * kEmitWarps;
+                const int2 e = k < nl ? c.blk_list[l0 + k] : make_int2(-1, 0);
+                const int ne = min(32, (nl - k0 + kEmitWarps - 1) / kEmitWarps);  // (warp-uniform)
+                for (int u = 0; u < ne; ++u) {
+                    const int m = __shfl_sync(kFull, e.x, u);
+                    const int pk = __shfl_sync(kFull, e.y, u);
+                    const int rel = (pk & 0xfff) - 32 + lane;
+                    if (m >= 0 && lane < (pk >> 12) && rel >= 0 && rel < cnt_b) {
+                        cp_async<(int)sizeof(KeyT)>(&sk[rel], ckey + (int64_t)m * CH + lane);
+                        cp_async<4>(&si[rel], c.chunk_data + (int64_t)m * CH + lane);
+                    }
+                }
+            }
+            cp_async_commit();
+            cp_async_wait_all();
+        }
+        for (int k0 = wid; sizeof(KeyT) < 4 && k0 < nl; k0 += kEmitWarps * kEmitBatch) {
             int2 e = make_int2(-1, 0);
             if (lane < kEmitBatch) {
                 const int k = k0 + lane * kEmitWarps;
