@@ -322,7 +322,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
                          const int64_t *d_offsets, const int32_t *d_roots, int M, cudaStream_t s,
                          int sms, int64_t *launches, bool small_lists, int stop_after) {
     NvtxRange whole("pbit_sort");
-    int64_t n = 0;  // kernel launches
+    const int64_t n0 = g_enqueued_launches;  // kernel launches of this call = the difference
     prof_begin(s);
     if (ms.count < 0)
         return PBIT_ENOMEM;
@@ -352,7 +352,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
             g_prof.small = true;
         }
         if (launches)
-            *launches = 4;
+            *launches = g_enqueued_launches - n0;
         return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
     }
     if (g_prof.on)
@@ -361,15 +361,12 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
     {
         NvtxRange r("pbit_rank");
         launch_pack(cc, s, sms);
-        if (cc.pack)
-            ++n;
         launch_walk(cc, s, sms);
         launch_wyllie(cc, s, sms, rounds);
         launch_validate_emit(cc, s, sms);
     }
     if (stop_after == 1)
         return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
-    n += 11 + rounds - cc.emit_hist;  // (the emit is four kernels)
     const int iters = (M + cc.D - 1) / cc.D;
     {
         NvtxRange r("pbit_msd_passes");
@@ -380,13 +377,11 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
                 return cudaGetLastError() == cudaSuccess ? PBIT_OK : PBIT_ECUDA;
         }
     }
-    n += iters * launches_per_iteration();
     {
         NvtxRange r("pbit_finish_relink");
         launch_check_done(cc, iters, s);
         launch_finish_relink(cc, s, sms);
     }
-    n += 4;
     if (g_prof.on) {
         g_prof.rcap = cc.Rcap;
         g_prof.scap = cc.Scap;
@@ -397,7 +392,7 @@ pbit_status enqueue_sort(const Ctx &c, const MemsetList &ms, int mode, const Lis
         g_prof.pack = cc.pack != nullptr;
     }
     if (launches)
-        *launches = n;
+        *launches = g_enqueued_launches - n0;
     if (cudaGetLastError() != cudaSuccess)
         return PBIT_ECUDA;
     return PBIT_OK;

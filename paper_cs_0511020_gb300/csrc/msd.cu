@@ -1064,7 +1064,6 @@ void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms) {
     }
 }
 
-int64_t launches_per_iteration() { return 8; }
 int pass_tile() { return kTile; }
 int stat_tile() { return kTile; }
 int digit_bits() { return kD; }

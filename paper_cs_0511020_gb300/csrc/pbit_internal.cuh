@@ -334,6 +334,10 @@ __device__ __forceinline__ KeyT sort_key(KeyT k, int flags, int M) {
 // another kernel the wait returns at once.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Kernels enqueued by this host thread through launch_pdl (a sort call
+// reports the difference across its enqueue as its launch count).
+inline thread_local int64_t g_enqueued_launches = 0;
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args &&...args) {
@@ -347,6 +351,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
+    ++g_enqueued_launches;
     return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
@@ -453,7 +458,6 @@ void launch_iteration(const Ctx &c, int it, cudaStream_t s, int sms);   // D <= 
 void launch_iteration8(const Ctx &c, int it, cudaStream_t s, int sms);  // windows of 5..8 bits (msd8.cu)
 void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms);
 void launch_check_done(const Ctx &c, int iters, cudaStream_t s);
-int64_t launches_per_iteration();
 int finish_capacity();
 bool relink_blocked(const Ctx &c);
 int relink_bucket_bits(const Ctx &c);
