@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
                         tot += cw[x];
                     }
                     int ttot;
-                    uint32_t run = (uint32_t)block_excl_scan((int)tot, &ttot, S.sh);
+                    uint32_t run = (uint32_t)block_excl_scan_1bar((int)tot, &ttot, S.sh);
 #pragma unroll
                     for (int x = 0; x < kMidWarps; ++x) {
                         S.wcnt[x][tid] = run;

@@ -398,7 +398,7 @@ __device__ __forceinline__ int32_t tile_base8(const Ctx &c, int cur, const Tile8
 // Returns the output bases of the next tile's digits (loaded meanwhile).
 template <typename KeyT, bool kWhole>
 __device__ __forceinline__ int32_t pass8_tile(const Ctx &c, int cur, Pass8Smem &S, unsigned char *stage, int st,
-                                              bool more, int32_t gb, int tid, int lane, int wid, unsigned lt) {
+                                              int T, int32_t gb, int tid, int lane, int wid, unsigned lt) {
     const Tile8 &t = S.tl[st];  // (fields read from shared memory where used)
     const int lo = t.lo, cnt = kWhole ? k8Tile : t.cnt;
     const unsigned dmask = (1u << (t.hi - t.lo)) - 1u;
@@ -438,6 +438,7 @@ __device__ __forceinline__ int32_t pass8_tile(const Ctx &c, int cur, Pass8Smem &
     }
     __syncthreads();
     // the next tile's output bases: loads in flight during the rest of this tile
+    const bool more = S.nt[st ^ 1] < T;
     const int32_t gb_next = more ? tile_base8(c, cur, S.tl[st ^ 1], tid) : 0;
     // ---- tile offsets per digit (thread tid = digit), each warp's first slot
     {
@@ -449,7 +450,7 @@ __device__ __forceinline__ int32_t pass8_tile(const Ctx &c, int cur, Pass8Smem &
             tot += cw[w];
         }
         int ttot;
-        uint32_t run = (uint32_t)block_excl_scan((int)tot, &ttot, S.sh);
+        uint32_t run = (uint32_t)block_excl_scan_1bar((int)tot, &ttot, S.sh);
         S.gdelta[tid] = gb - (int32_t)run;
 #pragma unroll
         for (int w = 0; w < k8Warps; ++w) {
@@ -574,35 +575,30 @@ __global__ void __launch_bounds__(k8TPB, Pass8Layout<KeyT>::kMinBlocks) k_pass8(
     int st = 0;
     while (g < T) {
         unsigned char *stage = stages + st * Pass8Layout<KeyT>::kStage;
-        if (tid == 0) {  // prefetch the next tile into the other stage, claim the one after
+        // one thread waits for the copy (acquire), the barrier publishes it;
+        // every thread is past the previous tile, so the other stage is free
+        const bool landed = (tid != 0) || mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
+        if (!__syncthreads_and(landed)) {
+            set_status(c.status, PBIT_ETIMEOUT);
+            if (tid == 0)  // wait (bounded) for the copy still in flight before leaving
+                mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
+            return;
+        }
+        phases ^= 1u << st;
+        if (tid == 0) {  // the next tile into the other stage (the others read its
+                         // description after the tile's first barrier), claim the one after
             S.nt[st ^ 1] = claim;
             if (claim < T) {
                 pass8_issue<KeyT>(c, cur, A, claim, st ^ 1, q, S, stages + (st ^ 1) * Pass8Layout<KeyT>::kStage);
                 claim = atomicAdd(&c.ctr->tile_ctr[it], 1);
             }
         }
-        // one thread waits for the copy (acquire), the barrier publishes it
-        // (and the next tile's description)
-        const bool landed = (tid != 0) || mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
-        if (!__syncthreads_and(landed)) {
-            set_status(c.status, PBIT_ETIMEOUT);
-            if (tid == 0) {  // wait (bounded) for the copies still in flight before leaving
-                mbar_wait_bounded(&S.bar[st], (phases >> st) & 1u, 1ll << 26);
-                if (S.nt[st ^ 1] < T)
-                    mbar_wait_bounded(&S.bar[st ^ 1], (phases >> (st ^ 1)) & 1u, 1ll << 26);
-            }
-            return;
-        }
-        phases ^= 1u << st;
-        const int gnext = S.nt[st ^ 1];
-        const bool more = gnext < T;
         // (almost every tile is full: its copy of the code has no end checks)
         const int32_t gb_next = S.tl[st].cnt == k8Tile
-                                    ? pass8_tile<KeyT, true>(c, cur, S, stage, st, more, gb, tid, lane, wid, lt)
-                                    : pass8_tile<KeyT, false>(c, cur, S, stage, st, more, gb, tid, lane, wid, lt);
-        __syncthreads();
+                                    ? pass8_tile<KeyT, true>(c, cur, S, stage, st, T, gb, tid, lane, wid, lt)
+                                    : pass8_tile<KeyT, false>(c, cur, S, stage, st, T, gb, tid, lane, wid, lt);
         gb = gb_next;
-        g = gnext;
+        g = S.nt[st ^ 1];  // (written before the tile's barriers)
         st ^= 1;
     }
 }

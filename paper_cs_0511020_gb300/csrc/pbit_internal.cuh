@@ -268,6 +268,33 @@ __device__ __forceinline__ int block_excl_scan(int v, int *total, int *sh /* >= 
     return r;
 }
 
+// Exclusive scan over the block, one value per thread, with one barrier:
+// every warp scans its values, lane 31 posts the warp's total, and after the
+// barrier each thread adds the totals of the warps before its own.  sh (one
+// int per warp) must not be written again until the block has passed
+// another barrier.
+__device__ __forceinline__ int block_excl_scan_1bar(int v, int *total, int *sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o)
+            x += y;
+    }
+    if (lane == 31)
+        sh[wid] = x;
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+        const int t = sh[w];
+        before += w < wid ? t : 0;
+        tot += t;
+    }
+    *total = tot;
+    return before + x - v;
+}
+
 // Stable rank of one lane's element among the elements of its 32-element
 // group and of the warp's earlier groups that carry the same digit.  tab is
 // the warp's table in shared memory, one {peer mask, running count} pair per
