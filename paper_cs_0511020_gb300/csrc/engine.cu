@@ -292,6 +292,7 @@ size_t bind(const Sizes &z, unsigned char *ws, Ctx *c, MemsetList *ms) {
     x.plan_mid = (int32_t *)take(4 * (size_t)z.seg_cap);
     x.fin = (Fin *)take(sizeof(Fin) * (size_t)z.fin_cap);
     x.mid = (Fin *)take(sizeof(Fin) * (size_t)z.mid_cap);
+    x.mid_defer = (int32_t *)take(4 * (size_t)z.mid_cap);
     x.rel_cursor = (int32_t *)take(4 * (size_t)relink_max_buckets());
     zero(x.rel_cursor, 0, 4 * (size_t)relink_max_buckets());
     if (c)

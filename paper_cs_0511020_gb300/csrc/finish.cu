@@ -343,21 +343,26 @@ __global__ void __launch_bounds__(32 * kFWarps) k_finish(Ctx c) {
 // small-bucket finish that such a bucket would otherwise go through.
 constexpr int kMidTPB = 256;
 constexpr int kMidWarps = kMidTPB / 32;
-constexpr int kMidItems = kMidCap / kMidTPB;  // groups of 32 per warp slice, at most
 constexpr int kMidBits = 8;
 constexpr int kMidBins = 1 << kMidBits;
 static_assert(kMidBins == kMidTPB, "one thread per digit");
 
-template <typename KeyT>
+// Buffers for buckets of up to kCap nodes.  Keys of 4 and 8 bytes have two
+// copies of the kernel: one sized for kMidSmallCap nodes (nearly every
+// bucket the passes leave; its smaller buffers let more CTAs share an SM),
+// which defers larger buckets to the one sized for kMidCap.
+template <typename KeyT, int kCap>
 struct MidLayout {
-    static constexpr int kKeyBuf = kMidCap * (int)sizeof(KeyT) + 32;  // + room for the copy's 16-byte rounding
-    static constexpr int kIdxBuf = kMidCap * 4 + 32;
+    static constexpr int kKeyBuf = kCap * (int)sizeof(KeyT) + 32;  // + room for the copy's 16-byte rounding
+    static constexpr int kIdxBuf = kCap * 4 + 32;
     static constexpr int kBuf = ((kKeyBuf + kIdxBuf + 127) / 128) * 128;
     static constexpr int kTotal = 2 * kBuf;
-    static constexpr int kMinBlocks = sizeof(KeyT) == 8 ? 2 : 3;
+    static constexpr int kItems = kCap / kMidTPB;  // groups of 32 per warp slice, at most
+    static constexpr int kMinBlocks = kCap < kMidCap ? (sizeof(KeyT) == 8 ? 3 : 4) : (sizeof(KeyT) == 8 ? 2 : 3);
 };
 
-static_assert(kMidWarps * kMidBins * (int)sizeof(uint2) <= MidLayout<uint8_t>::kBuf,
+static_assert(kMidWarps * kMidBins * (int)sizeof(uint2) <= MidLayout<uint8_t, kMidCap>::kBuf &&
+                  kMidWarps * kMidBins * (int)sizeof(uint2) <= MidLayout<uint32_t, kMidSmallCap>::kBuf,
               "the ranking table fits in a bucket buffer");
 
 struct MidSmem {
@@ -368,31 +373,44 @@ struct MidSmem {
     alignas(8) uint64_t bar;
 };
 
-template <typename KeyT>
-__global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish_mid(Ctx c) {
+// kDeferred: the buckets the smaller copy left (their indices in mid_defer).
+template <typename KeyT, int kCap, bool kDeferred>
+__global__ void __launch_bounds__(kMidTPB, (MidLayout<KeyT, kCap>::kMinBlocks)) k_finish_mid(Ctx c) {
     griddep_wait();
     extern __shared__ __align__(128) unsigned char msm[];
     __shared__ MidSmem S;
     using U = typename KeyWord<KeyT>::U;
-    using L = MidLayout<KeyT>;
+    using L = MidLayout<KeyT, kCap>;
+    constexpr int kMidItems = L::kItems;
+    constexpr bool kDefers = kCap < kMidCap;  // larger buckets go to the kDeferred copy
     if (*(volatile int32_t *)c.status)
         return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned lt = lanemask_lt(), lane_bit = 1u << lane;
-    const int nmid = c.ctr->mid_count;
+    const int nmid = kDeferred ? c.ctr->defer_count : c.ctr->mid_count;
+    int32_t *claim_ctr = kDeferred ? &c.ctr->fin_ctr2.v : &c.ctr->fin_ctr.v;
     unsigned char *bufA = msm, *bufB = msm + L::kBuf;
     if (tid == 0) {
         mbar_init(&S.bar, 1);
         fence_mbar_init();
-        S.next = atomicAdd(&c.ctr->fin_ctr.v, 1);
+        S.next = atomicAdd(claim_ctr, 1);
     }
     __syncthreads();
     uint32_t phase = 0;
     long long my_elems = 0;
     for (int m = S.next; m < nmid; m = S.next) {
-        const Fin f = c.mid[m];
+        const Fin f = c.mid[kDeferred ? c.mid_defer[m] : m];
         const int len = f.len, hi = f.hi;
-        const bool ok_len = len > 0 && len <= kMidCap;
+        if (kDefers && len > kCap) {  // (CTA-uniform) for the larger copy
+            __syncthreads();  // every thread has read m
+            if (tid == 0) {
+                c.mid_defer[atomicAdd(&c.ctr->defer_count, 1)] = m;
+                S.next = atomicAdd(claim_ctr, 1);
+            }
+            __syncthreads();
+            continue;
+        }
+        const bool ok_len = len > 0 && len <= kCap;
         constexpr int W = (int)sizeof(KeyT);
         int shk = 0, shi = 0;
         {
@@ -422,7 +440,7 @@ __global__ void __launch_bounds__(kMidTPB, MidLayout<KeyT>::kMinBlocks) k_finish
             return;
         }
         if (tid == 0)  // every thread has read m: claim the next bucket
-            S.next = atomicAdd(&c.ctr->fin_ctr.v, 1);
+            S.next = atomicAdd(claim_ctr, 1);
         if (!ok_len) {  // (a planning error: cannot happen)
             set_status(c.status, kStOverflow);
             __syncthreads();
@@ -820,13 +838,31 @@ __global__ void k_check_done(Ctx c, int iters) {
 template <typename KeyT>
 static void launch_finish_t(const Ctx &c, cudaStream_t s, int sms) {
     {
-        const int smem = MidLayout<KeyT>::kTotal;
-        cudaFuncSetAttribute(k_finish_mid<KeyT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        const int per_sm = MidLayout<KeyT>::kMinBlocks;  // (registers and shared memory allow this many)
-        static_assert(3 * (MidLayout<uint32_t>::kTotal + (int)sizeof(MidSmem) + 1024) <= 228 * 1024, "3 CTAs per SM");
-        static_assert(2 * (MidLayout<unsigned long long>::kTotal + (int)sizeof(MidSmem) + 1024) <= 228 * 1024,
-                      "2 CTAs per SM");
-        launch_pdl(k_finish_mid<KeyT>, dim3((unsigned)(sms * per_sm)), dim3(kMidTPB), smem, s, c);
+        using LB = MidLayout<KeyT, kMidCap>;
+        using LS = MidLayout<KeyT, kMidSmallCap>;
+        static_assert(3 * (MidLayout<uint32_t, kMidCap>::kTotal + (int)sizeof(MidSmem) + 1024) <= 228 * 1024 &&
+                          4 * (MidLayout<uint32_t, kMidSmallCap>::kTotal + (int)sizeof(MidSmem) + 1024) <= 228 * 1024,
+                      "3 (4) CTAs per SM");
+        static_assert(2 * (MidLayout<unsigned long long, kMidCap>::kTotal + (int)sizeof(MidSmem) + 1024) <= 228 * 1024 &&
+                          3 * (MidLayout<unsigned long long, kMidSmallCap>::kTotal + (int)sizeof(MidSmem) + 1024) <=
+                              228 * 1024,
+                      "2 (3) CTAs per SM");
+        // (registers and shared memory allow kMinBlocks CTAs per SM)
+        if constexpr (sizeof(KeyT) >= 4) {
+            cudaFuncSetAttribute(k_finish_mid<KeyT, kMidSmallCap, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, LS::kTotal);
+            launch_pdl(k_finish_mid<KeyT, kMidSmallCap, false>, dim3((unsigned)(sms * LS::kMinBlocks)), dim3(kMidTPB),
+                       LS::kTotal, s, c);
+            cudaFuncSetAttribute(k_finish_mid<KeyT, kMidCap, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 LB::kTotal);
+            launch_pdl(k_finish_mid<KeyT, kMidCap, true>, dim3((unsigned)(sms * LB::kMinBlocks)), dim3(kMidTPB),
+                       LB::kTotal, s, c);
+        } else {
+            cudaFuncSetAttribute(k_finish_mid<KeyT, kMidCap, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 LB::kTotal);
+            launch_pdl(k_finish_mid<KeyT, kMidCap, false>, dim3((unsigned)(sms * LB::kMinBlocks)), dim3(kMidTPB),
+                       LB::kTotal, s, c);
+        }
     }
     const int smem = (int)(kFWarps * 2 * kFinCap * (sizeof(KeyT) + 4));
     const int per_sm = max(1, min(16, (200 * 1024) / smem));

@@ -60,6 +60,7 @@ constexpr int kMaxIters = 64;
 // Buckets of (cutoff, kMidCap] nodes are finished by one CTA each in shared
 // memory instead of going through further global passes.
 constexpr int kMidCap = 4096;
+constexpr int kMidSmallCap = 2560;  // buckets up to this size: a CTA finish sized for them (more CTAs per SM)
 constexpr int kMidSpan = 16;
 // Lists of at most kSmallList nodes are sorted by one kernel, one CTA each.
 constexpr int kSmallList = 4096;  // ... when at most this many of their key bits vary (4 windows)
@@ -85,10 +86,12 @@ struct Counters {
     HotCounter chunk_next;     // bump allocator of ranking chunks
     HotCounter task_next;      // work counter of the ranking walk
     HotCounter fin_ctr;        // work counter of the CTA finish
+    HotCounter fin_ctr2;       // work counter of the CTA finish of the deferred (largest) buckets
     HotCounter rel_ctr;        // work counter of the relink partition
     int32_t n_virt;            // total nodes over all lists
     int32_t fin_count;
     int32_t mid_count;         // buckets finished by one CTA each
+    int32_t defer_count;       // of those, left by the smaller CTA finish for the larger one
     int32_t act_count[2];
     int32_t pend_count[2];
     int32_t num_tiles[2];
@@ -180,6 +183,7 @@ struct Ctx {
     int32_t *plan_mid;          // seg_cap per-segment mid-bucket counts -> offsets
     Fin *fin;
     Fin *mid;                   // mid_cap buckets of (cutoff, kMidCap] nodes: one CTA each
+    int32_t *mid_defer;         // mid_cap: indices into mid of the buckets above kMidSmallCap nodes
     int64_t mid_cap;
     int32_t *rel_cursor;        // blocked relink: pairs per node block
     int32_t *new_roots;

@@ -350,6 +350,35 @@ def test_mid_size_buckets_batched(pb):
         assert (got[a:b] == np.where(want >= 0, want + a, -1)).all(), f"list {i}"
 
 
+@pytest.mark.parametrize("kb", [4, 8])
+def test_mid_size_buckets_both_capacities(pb, kb):
+    """Keys of 4 and 8 bytes: buckets of up to 2560 nodes are finished by the
+    CTA finish sized for them, larger ones (up to 4096) are deferred to the
+    one sized for 4096; a batch with lengths on both sides of 2560."""
+    lens = np.array([513, 2559, 2560, 2561, 3000, 4095, 4096, 700, 2048, 1] * 4, dtype=np.int64)
+    nxt, key, roots, off = I.batched_pool(lens, kb, 212 + kb)
+    d_next = torch.from_numpy(nxt.copy()).cuda()
+    nr = pb.sort_lists_batched(d_next, _dev_key(key), torch.from_numpy(roots).cuda(),
+                               torch.from_numpy(off).cuda(), M=16, K=4)
+    got, nr = d_next.cpu().numpy(), nr.cpu().numpy()
+    for i in range(lens.size):
+        a, b = off[i], off[i + 1]
+        sub_next = np.where(nxt[a:b] >= 0, nxt[a:b] - a, -1).astype(np.int32)
+        want, wr, _ = O.pbit_sort(sub_next, key[a:b], roots[i] - a, 16, 4)
+        assert nr[i] == wr + a
+        assert (got[a:b] == np.where(want >= 0, want + a, -1)).all(), f"list {i}"
+
+
+@pytest.mark.parametrize("n", [600_000, 700_000])
+def test_mid_buckets_after_a_pass(pb, n):
+    """Keys below 2^20: one 8-bit pass leaves 256 buckets of n / 256 nodes with
+    12 bits to sort (about 2340 nodes at 600 000: the smaller CTA finish;
+    about 2730 at 700 000: deferred to the larger one)."""
+    nxt, root = I.random_list(n, 215 + n)
+    key = I.uniform_keys(n, 4, 216 + n) & np.uint32((1 << 20) - 1)
+    _check_vs_oracle(pb, nxt, key, root, 32, tune={"digit_bits": 8})
+
+
 @pytest.mark.parametrize("n", [1, 2, 33, 1000, 4095, 4096])
 @pytest.mark.parametrize("kb", [1, 2, 4, 8])
 def test_short_list_kernel(pb, n, kb):
