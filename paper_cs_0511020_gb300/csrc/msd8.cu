@@ -332,8 +332,9 @@ struct Pass8Layout {
     static constexpr int kIdxBytes = k8Tile * 4 + 32;
     static constexpr int kStage = ((kKeyBytes + kIdxBytes + 127) / 128) * 128;
     static constexpr int kHdr = ((int)sizeof(Pass8Smem) + 127) / 128 * 128;
-    static constexpr int kTotal = kHdr + 2 * kStage;
-    static constexpr int kMinBlocks = 3;  // (at 4 the registers spill: measured slower)
+    static constexpr int kIdx2 = kHdr + 2 * kStage;  // the tile's node ids in digit order
+    static constexpr int kTotal = kIdx2 + k8Tile * 4;
+    static constexpr int kMinBlocks = sizeof(KeyT) == 8 ? 3 : 4;
 };
 
 __device__ __forceinline__ void cursor_seek(const Ctx &c, int cur, int A, int g, SegCursor &q) {
@@ -408,7 +409,6 @@ __device__ __forceinline__ int32_t pass8_tile(const Ctx &c, int cur, Pass8Smem &
 
     // ---- ranking within the warp
     KeyT key[k8Items];
-    int32_t idx[k8Items];
     uint32_t rnk[k8Items];
     uint32_t *wc = S.wcnt[wid];
 #pragma unroll
@@ -416,7 +416,6 @@ __device__ __forceinline__ int32_t pass8_tile(const Ctx &c, int cur, Pass8Smem &
         const int pos = wid * (32 * k8Items) + i * 32 + lane;
         const bool valid = kWhole || pos < cnt;
         key[i] = valid ? sk[pos] : (KeyT)0;
-        idx[i] = valid ? si[pos] : 0;
         const unsigned dig = digit_of<KeyT>(key[i], lo, dmask);
         // peers: the valid lanes that differ from this one in no digit bit
         // (bits above a narrower window are 0 everywhere)
@@ -459,9 +458,10 @@ __device__ __forceinline__ int32_t pass8_tile(const Ctx &c, int cur, Pass8Smem &
         }
     }
     __syncthreads();
-    // ---- local scatter into the stage buffer (all items are in registers)
+    // ---- local scatter: keys into the stage buffer (all of them are in
+    // registers), node ids from the stage into a buffer of their own
     KeyT *ok = reinterpret_cast<KeyT *>(stage);
-    int32_t *oi = reinterpret_cast<int32_t *>(stage + Pass8Layout<KeyT>::kKeyBytes);
+    int32_t *oi = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(&S) + Pass8Layout<KeyT>::kIdx2);
 #pragma unroll
     for (int i = 0; i < k8Items; ++i) {
         const int pos = wid * (32 * k8Items) + i * 32 + lane;
@@ -470,7 +470,7 @@ __device__ __forceinline__ int32_t pass8_tile(const Ctx &c, int cur, Pass8Smem &
         bad |= (kWhole || pos < cnt) && !in;
         if ((kWhole || pos < cnt) && in) {
             ok[lp] = key[i];
-            oi[lp] = idx[i];
+            oi[lp] = si[pos];
         }
     }
     __syncthreads();
