@@ -644,6 +644,8 @@ __device__ __forceinline__ void relink_issue(const Ctx &c, int g, int st, int32_
 // Tiles of kRelTile sorted positions are claimed from a counter one step
 // ahead; the bulk copy engine brings each tile's order entries (and the one
 // after it) into shared memory while the previous tile is bucketed.
+// kOne: a single list (its descriptor is read once); kDoubly: prev[] too.
+template <bool kOne, bool kDoubly>
 __global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
     griddep_wait();
     extern __shared__ __align__(16) unsigned char rel_smem[];
@@ -654,8 +656,10 @@ __global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
     const int32_t nv = c.ctr->n_virt;
     const int L = c.num_lists;
     const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
-    const bool doubly = (c.flags & PBIT_DOUBLY) != 0;
     const int T = (int)((nv + kRelTile - 1) / kRelTile);
+    ListDesc d1{};
+    if constexpr (kOne)
+        d1 = c.desc[0];
     int32_t *tv = c.idxb[0], *ts = c.idxb[1];
     int claim = 0;  // thread 0: the tile claimed for the next issue
     if (threadIdx.x == 0) {
@@ -703,17 +707,17 @@ __global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
             vv[i] = -1;
             ss[i] = -1;
             if (q < nv) {
-                const int lst = L == 1 ? 0 : upper_index(c.out_base, L, (int32_t)q);
-                const ListDesc &d = c.desc[lst];
+                const int lst = kOne ? 0 : upper_index(c.out_base, L, (int32_t)q);
+                const ListDesc &d = kOne ? d1 : c.desc[lst];
                 const int32_t loc = fs[e] - d.out_base;
                 const int64_t end = (int64_t)d.out_base + d.n;
                 int32_t succ = -1;
-                bool bad = loc < 0 || loc >= d.n;
+                bool bad = (uint32_t)loc >= (uint32_t)d.n;
                 if (q + 1 < end) {
                     const int32_t ls = fs[e + 1] - d.out_base;
-                    bad |= ls < 0 || ls >= d.n;
+                    bad |= (uint32_t)ls >= (uint32_t)d.n;
                     succ = d.id_base + ls;
-                    if (doubly && !bad)
+                    if (kDoubly && !bad)
                         *(int32_t *)((unsigned char *)d.prev + (int64_t)succ * d.prev_stride) = d.id_base + loc;
                 }
                 if (bad) {
@@ -723,7 +727,7 @@ __global__ void __launch_bounds__(kRelTPB, 4) k_relink_part(Ctx c, int rb) {
                     ss[i] = succ;
                     if (q == d.out_base) {
                         c.new_roots[lst] = vv[i];
-                        if (doubly)
+                        if (kDoubly)
                             *(int32_t *)((unsigned char *)d.prev + (int64_t)vv[i] * d.prev_stride) = -1;
                     }
                 }
@@ -881,8 +885,11 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
         const int rb = relink_bucket_bits(c);
         const int64_t pblocks = min((int64_t)sms * 4, max((int64_t)1, (c.ncap + kRelTile - 1) / kRelTile));
         const int smem = (int)sizeof(RelSmem);
-        cudaFuncSetAttribute(k_relink_part, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        launch_pdl(k_relink_part, dim3((unsigned)pblocks), dim3(kRelTPB), smem, s, c, rb);
+        const bool one = c.num_lists == 1, doubly = (c.flags & PBIT_DOUBLY) != 0;
+        auto part = one ? (doubly ? k_relink_part<true, true> : k_relink_part<true, false>)
+                        : (doubly ? k_relink_part<false, true> : k_relink_part<false, false>);
+        cudaFuncSetAttribute(part, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        launch_pdl(part, dim3((unsigned)pblocks), dim3(kRelTPB), smem, s, c, rb);
         const int64_t ablocks = min((int64_t)sms * 8, (int64_t)(((1ll << rb) / 16 + 255) / 256));
         const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
         for (int b = 0; b < nb; ++b)
