@@ -535,6 +535,34 @@ static pbit_status sort_pool(const pbit_pool *pool, int32_t num_lists, const int
     return finish_call(c, host_root, s);
 }
 
+// The host-buffer call's copy of next[] back to the host, one relink window
+// at a time (RelinkWindowHook): stream cs waits for the window's kernel on
+// the sort stream, then copies the window's bytes.
+struct WindowCopy {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    const unsigned char *dnext = nullptr;
+    unsigned char *hnext = nullptr;
+    int64_t stride = 4, n = 0, copied = 0;  // copied: nodes whose window is on its way
+    size_t bytes = 0;                       // next[] span in bytes
+    bool ok = false;
+};
+
+static void copy_window(void *arg, int64_t lo, int64_t hi, cudaStream_t s) {
+    WindowCopy &w = *static_cast<WindowCopy *>(arg);
+    if (!w.ok || lo != w.copied || hi > w.n || hi <= lo) {
+        w.ok = false;
+        return;
+    }
+    const size_t b0 = (size_t)(lo * w.stride), b1 = hi == w.n ? w.bytes : (size_t)(hi * w.stride);
+    if (cudaEventRecord(w.ev, s) != cudaSuccess || cudaStreamWaitEvent(w.cs, w.ev, 0) != cudaSuccess ||
+        cudaMemcpyAsync(w.hnext + b0, w.dnext + b0, b1 - b0, cudaMemcpyDeviceToHost, w.cs) != cudaSuccess) {
+        w.ok = false;
+        return;
+    }
+    w.copied = hi;
+}
+
 PoolSpan pool_span(const pbit_pool *p) {
     PoolSpan r{};
     const int64_t n = p->pool_size;
@@ -760,11 +788,34 @@ pbit_status pbit_sort_list_host(const pbit_pool *host_pool, int32_t root, int64_
         return PBIT_ECUDA;
     Ctx c;
     const size_t rest = ws_bytes - (size_t)(w - (unsigned char *)ws);
+    // next[] goes back window by window on a second stream, each window as
+    // soon as the relink kernel that writes it has run (copied back
+    // unconditionally: on an error the device copy was not written)
+    WindowCopy wc{};
+    wc.dnext = dnext;
+    wc.hnext = (unsigned char *)host_pool->next;
+    wc.stride = host_pool->next_stride_bytes;
+    wc.n = n;
+    wc.bytes = sp.next_bytes;
+    wc.ok = cudaStreamCreateWithFlags(&wc.cs, cudaStreamNonBlocking) == cudaSuccess;
+    wc.ok = wc.ok && cudaEventCreateWithFlags(&wc.ev, cudaEventDisableTiming) == cudaSuccess;
+    if (wc.ok)
+        g_relink_hook = RelinkWindowHook{copy_window, &wc};
     pbit_status rc = enqueue_pool(&dp, 1, nullptr, nullptr, root, n, M, K, nullptr, tune, w, rest, s, &c);
+    g_relink_hook = RelinkWindowHook{};
+    bool copied = false;
+    if (wc.ok && wc.copied == n) {  // every window is on its way: s waits for the copies
+        copied = cudaEventRecord(wc.ev, wc.cs) == cudaSuccess && cudaStreamWaitEvent(s, wc.ev, 0) == cudaSuccess;
+    }
+    if (!copied && wc.cs)  // (no windows, or a window's copy failed: everything again on s)
+        cudaStreamSynchronize(wc.cs);
+    if (wc.ev)
+        cudaEventDestroy(wc.ev);
+    if (wc.cs)
+        cudaStreamDestroy(wc.cs);  // (released once its copies are done)
     if (rc != PBIT_OK)
         return rc;
-    // copy back unconditionally: on an error the device copy was not written
-    if (cudaMemcpyAsync(host_pool->next, dnext, sp.next_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (!copied && cudaMemcpyAsync(host_pool->next, dnext, sp.next_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return PBIT_ECUDA;
     if (sp.prev_bytes &&
         cudaMemcpyAsync(host_pool->prev, dprev, sp.prev_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)

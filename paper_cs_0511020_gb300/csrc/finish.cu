@@ -892,8 +892,11 @@ void launch_finish_relink(const Ctx &c, cudaStream_t s, int sms) {
         launch_pdl(part, dim3((unsigned)pblocks), dim3(kRelTPB), smem, s, c, rb);
         const int64_t ablocks = min((int64_t)sms * 8, (int64_t)(((1ll << rb) / 16 + 255) / 256));
         const int nb = (int)((c.ncap + (1ll << rb) - 1) >> rb);
-        for (int b = 0; b < nb; ++b)
+        for (int b = 0; b < nb; ++b) {
             launch_pdl(k_relink_apply, dim3((unsigned)ablocks), dim3(256), 0, s, c, rb, b);
+            if (g_relink_hook.fn)
+                g_relink_hook.fn(g_relink_hook.arg, (int64_t)b << rb, min(((int64_t)b + 1) << rb, c.ncap), s);
+        }
     } else {
         const int64_t blocks = min((int64_t)sms * 16, max((int64_t)1, (c.ncap + 255) / 256));
         launch_pdl(k_relink, dim3((unsigned)blocks), dim3(256), 0, s, c);

@@ -369,6 +369,16 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 // reports the difference across its enqueue as its launch count).
 inline thread_local int64_t g_enqueued_launches = 0;
 
+// Host side: when set, called after the blocked relink has enqueued on s the
+// last kernel that writes next[] of pool nodes [lo, hi) (the host-buffer call
+// starts copying that part of next[] back while the other windows are
+// applied).
+struct RelinkWindowHook {
+    void (*fn)(void *arg, int64_t lo, int64_t hi, cudaStream_t s) = nullptr;
+    void *arg = nullptr;
+};
+inline thread_local RelinkWindowHook g_relink_hook;
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args &&...args) {
