@@ -132,7 +132,12 @@ pbit_status pbit_sort_lists_batched(const pbit_pool *pool, int32_t num_lists,
  * next[] (and prev[] with PBIT_DOUBLY) copied back; key[] is only read.
  * Same contract as pbit_sort_list otherwise; host_pool's pointers are host
  * pointers.  The workspace (device) must hold pbit_workspace_size_host()
- * bytes.  Synchronizes `stream`.
+ * bytes.  For a list sorted through the relink windows, next[] is copied back
+ * one window at a time on a stream the call creates (and destroys before it
+ * returns), each window as soon as the kernel that writes it has run on
+ * `stream`; without windows (short lists) or if that stream cannot be
+ * created, one copy on `stream` after the sort.  Either way every copy has
+ * completed when the call returns.  Synchronizes `stream`.
  */
 pbit_status pbit_workspace_size_host(const pbit_pool *host_pool, const pbit_tune *tune, size_t *bytes);
 pbit_status pbit_sort_list_host(const pbit_pool *host_pool, int32_t root, int64_t n, int32_t M, int32_t K,
