@@ -57,6 +57,24 @@ def test_2p26_u64_zipf_and_u8(pb):
     _sort_and_check(pb, nxt, I.uniform_keys(n, 1, I.SEED_BASE + 33), root, 8)
 
 
+def test_aos_pool_many_relink_windows(pb):
+    """An AoS pool {int32 next; uint32 key} of 2^26 + 3 nodes: the relink
+    windows of an 8-byte stride hold 2^21 nodes, so this list has 33 of them
+    and a last one of 3 nodes; the keys between the links are left as they
+    were."""
+    n = (1 << 26) + 3
+    nxt, root = I.random_list(n, I.SEED_BASE + 50)
+    key = I.uniform_keys(n, 4, I.SEED_BASE + 51)
+    nodes = torch.from_numpy(np.stack([nxt, key.view(np.int32)], axis=1)).cuda()
+    st, r = pb.sort_pool_list(pb.make_pool_aos(nodes), root, n, 32, 4, check=False)
+    assert st == pb.OK, pb.status_string(st)
+    got = nodes.cpu().numpy()
+    del nodes
+    torch.cuda.empty_cache()
+    assert (got[:, 1].view(np.uint32) == key).all()
+    O.check_sorted_list(nxt, root, np.ascontiguousarray(got[:, 0]), r, key, 32)
+
+
 def test_batched_4096_lists(pb):
     lens = I.config4_lengths(I.SEED_BASE + 4)
     nxt, key, roots, off = I.batched_pool(lens, 4, I.SEED_BASE + 40)
