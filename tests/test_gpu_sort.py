@@ -369,14 +369,16 @@ def test_mid_size_buckets_both_capacities(pb, kb):
         assert (got[a:b] == np.where(want >= 0, want + a, -1)).all(), f"list {i}"
 
 
+@pytest.mark.parametrize("kb", [4, 8])
 @pytest.mark.parametrize("n", [600_000, 700_000])
-def test_mid_buckets_after_a_pass(pb, n):
+def test_mid_buckets_after_a_pass(pb, n, kb):
     """Keys below 2^20: one 8-bit pass leaves 256 buckets of n / 256 nodes with
     12 bits to sort (about 2340 nodes at 600 000: the smaller CTA finish;
     about 2730 at 700 000: deferred to the larger one)."""
     nxt, root = I.random_list(n, 215 + n)
-    key = I.uniform_keys(n, 4, 216 + n) & np.uint32((1 << 20) - 1)
-    _check_vs_oracle(pb, nxt, key, root, 32, tune={"digit_bits": 8})
+    dt = np.uint32 if kb == 4 else np.uint64
+    key = I.uniform_keys(n, kb, 216 + n) & dt((1 << 20) - 1)
+    _check_vs_oracle(pb, nxt, key, root, 8 * kb, tune={"digit_bits": 8})
 
 
 @pytest.mark.parametrize("n", [1, 2, 33, 1000, 4095, 4096])
